@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched FP32 Peaceman-Rachford ADI step (libadi) on GB300.
+
+Workload (one "step" = one full PR step -- stage 1 over every x-line, stage 2 over every
+y-line -- of every member of the batch):
+    batched FP32 at 4096 x 4096 cells: one CFD and one MFD simulation of the layered
+    seismic medium (c 1500-4500 m/s in four layers times a seeded 10 % Gaussian, a 15 Hz
+    Ricker point source at the centre, h = 5 m, dt = cfl_max h / c_max).
+Metric: grid-point updates per second (cells x steps / s), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the batch ("replicas
+only": the scheme has no data-path collective); value = all ranks' updates / max time.
+--impl reference times the FP64 CPU oracle on the same workload (bounded per-step sample)
+on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+N_SIDE = 4096
+METRIC = "ADI grid-point updates/s (batched FP32 vs plain FP64, 4096^2); p50/p99 latency"
+UNIT = "updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=N_SIDE)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "adi_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return res
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if sm:
+            res["sm_mhz"] = float(np.median(sm))
+            res["sm_max_mhz"] = float(max(smax))
+            res["samples"] = len(sm)
+        res["reasons"] = sorted(reasons)
+        return res
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2006_07583_gb300", "csrc"))):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(ROOT, "paper_2006_07583_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_point():
+    """DRAM bytes per grid point per stage launch from the committed ncu summary, valid only
+    while the kernel sources are unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "line_solve_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_point"])
+
+
+def make_specs(side, steps):
+    from paper_2006_07583_gb300 import workloads as wl
+
+    return [wl.seismic_spec(wl.CFD, side, side, steps, h=5.0, seed=1),
+            wl.seismic_spec(wl.MFD, side, side, steps, h=5.0, seed=2)]
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores on the same workload.  Each step is a
+    bounded sample: one PR step of a 512-line horizontal strip of each simulation."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2006_07583_gb300 import workloads as wl
+
+    threads = os.cpu_count() or 1
+    strip = 512
+    specs = make_specs(args.side, args.steps)
+    # the strip keeps the full line length along x (the expensive direction of the line
+    # solves) and 512 cells along y
+    cases = []
+    for sp in specs:
+        su, sv, sw = wl.shapes(sp.method, sp.nx, strip)
+        c = sp.c[:su[0], :su[1]].copy()
+        cases.append((sp.method, sp.nx, strip, sp.h, sp.dt, c ** 2,
+                      np.zeros(su), np.zeros(sv), np.zeros(sw)))
+    pts = sum(nx * ny for _, nx, ny, *_ in cases)
+
+    def one():
+        for (m, nx, ny, h, dt, kap, U, V, W) in cases:
+            oracle.run(m, nx, ny, h, dt, kap, U, V, W, 1, threads=threads)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    val = pts * args.steps / el
+    emit({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+          "data": "synthetic",
+          "config": {"workload": "oracle sample: 512-row strips of the 4096^2 CFD+MFD seismic "
+                                 "batch", "global_batch": 2, "side": args.side,
+                     "parallelism": "host cores"},
+          "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                           "sample": "one PR step of a %dx%d strip of each simulation per step"
+                                     % (args.side, strip)},
+          "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return 0
+
+
+def cpu_baseline_sample(side):
+    """Oracle on the host cores on a bounded sample of the bench workload (a 256-row strip
+    of each 4096-wide simulation, one PR step), scaled to updates/s."""
+    import oracle
+    from paper_2006_07583_gb300 import workloads as wl
+
+    threads = os.cpu_count() or 1
+    strip = 256
+    pts = 0
+    t0 = time.perf_counter()
+    for sp in make_specs(side, 1):
+        su, sv, sw = wl.shapes(sp.method, sp.nx, strip)
+        c = sp.c[:su[0], :su[1]].copy()
+        oracle.run(sp.method, sp.nx, strip, sp.h, sp.dt, c ** 2, np.zeros(su), np.zeros(sv),
+                   np.zeros(sw), 1, threads=threads)
+        pts += sp.nx * strip
+    el = time.perf_counter() - t0
+    return {"value": pts / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "one PR step of a %dx%d strip of each of the two simulations "
+                      "(%.1f s of CPU wall time)" % (side, strip, el)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2006_07583_gb300 import adi
+
+    adi.lib()
+    specs = make_specs(args.side, args.steps)
+    sims = []
+    for sp in specs:
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32)
+        s.set_source(*sp.source.as_tuple())
+        sims.append(s)
+    batch = adi.Batch(sims)
+    stream = torch.cuda.Stream()
+    batch.set_stream(stream.cuda_stream)
+    pts = sum(sp.nx * sp.ny for sp in specs)
+
+    for _ in range(args.warmup):
+        batch.half_step(1)
+        batch.half_step(2)
+    stream.synchronize()
+
+    clocks = ClockSampler(local)
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(K):
+            batch.half_step(1)
+            ev[2 * k + 1].record(stream)
+            batch.half_step(2, write_natural=(k == K - 1))
+            ev[2 * k + 2].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    st1 = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)]
+    st2 = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(K)]
+    step_ms = [a + b for a, b in zip(st1, st2)]
+    total_ms = ev[0].elapsed_time(ev[2 * K])
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * pts * K / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the line-solve launch), algorithmic bytes:
+    # each stage reads the carried pressure, the velocity and alpha and writes the first two
+    # -> 5 words per grid point per launch (20 B in FP32).
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 5 * 4 * pts
+    avg1, avg2 = float(np.mean(st1)), float(np.mean(st2))
+    dom_ms = max(avg1, avg2)
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    tpp = ncu_traffic_per_point()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": (tpp * pts if tpp is not None else None),
+            "kernel": "line_solve (stage %d)" % (1 if avg1 >= avg2 else 2),
+            "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
+            "stage_ms": {"x_lines": avg1, "y_lines": avg2}}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+           "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batched FP32 PR-ADI, 1 CFD + 1 MFD seismic sim at "
+                                  "%dx%d cells" % (args.side, args.side),
+                      "global_batch": 2 * ws, "side": args.side,
+                      "parallelism": "replicas x%d" % ws, "l2": "inputs larger than L2",
+                      "h_m": 5.0, "source": "15 Hz Ricker"},
+           "latency_ms": {"p50_step": float(np.percentile(step_ms, 50)),
+                          "p99_step": float(np.percentile(step_ms, 99))},
+           "clocks": ck, "roofline": roof,
+           "gpu_launches": 2 * K}
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3))
+    if rank == 0 and not args.no_fp64:
+        out["fp64_plain"] = fp64_plain(adi, args.side)
+    batch.close()
+    for s in sims:
+        s.close()
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline_sample(args.side)
+    if rank == 0:
+        emit(out)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def e2e_leg(adi, torch, sims, batch, specs, n):
+    """Same metric through the public API with host buffers: every step uploads each
+    member's fields from pinned host memory (adi_set_fields), advances the batch one step
+    and reads the fields back (adi_read_fields); wall-clock timed."""
+    bufs = []
+    for sp in specs:
+        from paper_2006_07583_gb300 import workloads as wl
+
+        shp = wl.shapes(sp.method, sp.nx, sp.ny)
+        bufs.append([torch.zeros(s, dtype=torch.float64, pin_memory=True).numpy() for s in shp])
+    h2d = sum(sum(b.nbytes for b in bb) for bb in bufs)
+    batch.sync()
+    for s, bb in zip(sims, bufs):
+        s.read_into(*bb)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        for s, bb in zip(sims, bufs):
+            s.set_fields(*bb)
+        batch.step(1)
+        batch.sync()
+        for s, bb in zip(sims, bufs):
+            s.read_into(*bb)
+    el = time.perf_counter() - t0
+    pts = sum(sp.nx * sp.ny for sp in specs)
+    return {"value": pts * n / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": h2d, "steps": n}
+
+
+def fp64_plain(adi, side):
+    """The plain one-simulation-at-a-time FP64 GPU path on the same two simulations."""
+    import torch
+
+    specs = make_specs(side, 2)
+    tot_pts, tot_s = 0, 0.0
+    for sp in specs:
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP64)
+        s.set_source(*sp.source.as_tuple())
+        s.step(1)
+        s.sync()
+        t0 = time.perf_counter()
+        s.step(2)
+        s.sync()
+        tot_s += time.perf_counter() - t0
+        tot_pts += 2 * sp.nx * sp.ny
+        s.close()
+    return {"value": tot_pts / tot_s, "unit": UNIT, "steps": 2,
+            "workload": "one sim at a time, FP64, %dx%d CFD then MFD" % (side, side)}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

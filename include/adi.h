@@ -1,0 +1,153 @@
+/*
+ * adi.h -- C ABI of libadi, a GB300 (sm_103a) engine for the Peaceman-Rachford ADI time
+ * step of the two 2-D acoustic schemes of Otero, Rojas, Moya and Castillo (arXiv
+ * 2006.07583):
+ *   ADI_CFD  fourth-order compact finite differences on the nodal mesh (Sec. 2.1, Eq. 4,
+ *            App. A), one coupled line system per grid line (Eq. 8, Eq. 10);
+ *   ADI_MFD  fourth-order mimetic divergence/gradient on the staggered mesh (Sec. 2.2,
+ *            Eq. 12, App. B).
+ * One time step is stage 1 (Eq. 6: implicit along every x-line) followed by stage 2
+ * (Eq. 7: implicit along every y-line).  The line systems are solved exactly, i.e. the
+ * library returns the fixed point of the paper's ADI iteration (Eq. 9).
+ *
+ * Conventions shared by every entry point
+ *   - Grids have nx cells along x and ny along y, square cells of side h.  Arrays are
+ *     row-major with i (row) the y index and j (column) the x index.
+ *       CFD: U, V, W are (ny+1) x (nx+1) node arrays.
+ *       MFD: U is (ny+2) x (nx+2) (cell centres plus the four edges), V is
+ *            (ny+2) x (nx+1) (x-nodes), W is (ny+1) x (nx+2) (y-nodes); U's corners are
+ *            unused.
+ *     The wave speed c is given where U lives; density is 1 and kappa = c^2.
+ *   - Dirichlet data: the pressure values on U's outer rows and columns at creation are
+ *     held fixed for the whole run (time-independent walls; zero for a free surface).
+ *   - nx, ny >= 16 (ADI_MIN_CELLS) and <= ADI_MAX_CELLS.
+ *   - Every function returns an adi_status (0 = ADI_OK).  Errors from device work are
+ *     sticky per handle: once a kernel fails, later calls on that handle return the same
+ *     code until the handle is destroyed.
+ *   - Input arrays are copied; the library owns all device memory it allocates; output
+ *     buffers belong to the caller.  A handle is not thread-safe; distinct handles are.
+ */
+#ifndef ADI_H
+#define ADI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADI_MIN_CELLS 16
+#define ADI_MAX_CELLS 16384
+
+typedef enum { ADI_CFD = 0, ADI_MFD = 1 } adi_method;
+typedef enum { ADI_FP32 = 0, ADI_FP64 = 1 } adi_precision;
+
+typedef enum {
+    ADI_OK = 0,
+    ADI_EINVAL = 1,      /* bad argument: sizes, h/dt <= 0, c <= 0, NaN input, bad index */
+    ADI_ENOMEM = 2,      /* device allocation failed or the request exceeds a budget     */
+    ADI_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed                  */
+    ADI_ENONFINITE = 4,  /* a field became NaN/Inf (checked by adi_check_finite)         */
+    ADI_ETIMEOUT = 5,    /* a bounded wait ran out                                       */
+    ADI_EBUSY = 6,       /* the object is in use (e.g. a member of a live batch)         */
+    ADI_ENOTSUP = 7,     /* no usable CUDA device / unsupported configuration            */
+    ADI_ESINGULAR = 8    /* a line system's precomputed pivot block was singular         */
+} adi_status;
+
+typedef struct adi_sim *adi_handle;
+typedef struct adi_batch_t *adi_batch;
+
+/* Version of this ABI (bumped on incompatible change). */
+int adi_abi_version(void);
+const char *adi_strerror(int code);
+
+/*
+ * adi_create -- one simulation resident on the current CUDA device.
+ *   method     ADI_CFD or ADI_MFD.
+ *   nx, ny     cells along x and y (16 .. 16384).
+ *   h, dt      cell side and time step, both > 0 and finite.
+ *   c_field    host, wave speed at U's points (shape as U), every value > 0; copied.
+ *   u0,v0,w0   host initial fields (shapes above) or NULL for zeros; u0's outer rows and
+ *              columns are the Dirichlet data.  Copied.
+ *   precision  ADI_FP32 (bulk arithmetic FP32, per-line factors precomputed in FP64) or
+ *              ADI_FP64.
+ * The simulation clock starts at t = 0.  On failure *out is NULL.
+ * Device memory: about (4 fields + 2 output fields) x points x sizeof(real) plus the line
+ * scratch; adi_state_bytes() reports the exact figure.
+ */
+int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
+               const double *c_field, const double *u0, const double *v0, const double *w0,
+               int precision);
+
+/* Exact device bytes adi_create would allocate for this configuration (0 if invalid). */
+size_t adi_state_bytes(int method, int nx, int ny, int precision);
+
+/*
+ * adi_set_source -- Ricker point source s(t) = amp (1 - 2 pi^2 f0^2 tau^2)
+ * exp(-pi^2 f0^2 tau^2), tau = t - tdelay, added as the forcing f = s(t)/h^2 of Eq. 1 at
+ * the interior pressure point U[is][js] (Eq. 5-7 source terms A_F at t_m and t_{m+1}).
+ * is, js must index an interior pressure point.  Replaces any previous source.
+ */
+int adi_set_source(adi_handle sim, int is, int js, double amp, double f0, double tdelay);
+
+/* adi_set_stream -- CUDA stream (cudaStream_t, NULL = legacy default) for later calls. */
+int adi_set_stream(adi_handle sim, void *cuda_stream);
+
+/*
+ * adi_step -- enqueue nsteps >= 0 full time steps (stage 1 then stage 2 each) on the
+ * handle's stream.  Asynchronous: returns after launching.  For nsteps >= 2 the step
+ * loop is captured once into a CUDA graph and replayed.
+ */
+int adi_step(adi_handle sim, int nsteps);
+
+/* adi_sync -- wait for the handle's stream; returns the first sticky error. */
+int adi_sync(adi_handle sim);
+
+/*
+ * adi_read_fields -- synchronise and copy the current (U, V, W) into caller-owned host
+ * buffers with the shapes above (any pointer may be NULL to skip that field).
+ */
+int adi_read_fields(adi_handle sim, double *u, double *v, double *w);
+
+/*
+ * adi_set_fields -- replace the current (U, V, W) by host arrays (shapes above; NULL keeps
+ * that field) and rebuild the carried stage-1 state (Eq. 8's A and W* of Alg. 1/2) at the
+ * current simulation time.  U's outer rows/columns become the new Dirichlet data.
+ */
+int adi_set_fields(adi_handle sim, const double *u, const double *v, const double *w);
+
+/* adi_check_finite -- scans U, V, W on the device; ADI_ENONFINITE if any is NaN/Inf. */
+int adi_check_finite(adi_handle sim);
+
+/* Completed steps and the simulation time t = steps * dt. */
+int adi_get_time(adi_handle sim, long long *steps, double *t);
+
+/* adi_destroy -- frees everything the handle owns (NULL is accepted). */
+int adi_destroy(adi_handle sim);
+
+/*
+ * Batching.  adi_batch_create groups n >= 1 simulations of one precision (any mix of
+ * methods and sizes) so that every half step of all of them runs as ONE kernel launch
+ * over a table of line descriptors (uneven lines from many simulations).  Members stay
+ * valid handles but must not be stepped individually while the batch lives (ADI_EBUSY).
+ * adi_batch_step(b, k) advances every member by k steps on the batch's stream, captured
+ * as a CUDA graph.
+ */
+int adi_batch_create(adi_batch *out, const adi_handle *sims, int n);
+int adi_batch_set_stream(adi_batch b, void *cuda_stream);
+int adi_batch_step(adi_batch b, int nsteps);
+int adi_batch_sync(adi_batch b);
+/*
+ * adi_batch_half_step -- enqueue ONE stage for every member: stage 1 (Eq. 6, all x-lines)
+ * or stage 2 (Eq. 7, all y-lines); write_natural != 0 makes stage 2 also refresh the
+ * natural u, w that adi_read_fields returns.  A full step is stage 1 then stage 2; the
+ * caller must issue them in that order (used to time each kernel separately).
+ */
+int adi_batch_half_step(adi_batch b, int stage, int write_natural);
+int adi_batch_destroy(adi_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADI_H */

@@ -1,0 +1,204 @@
+"""ctypes binding of libadi (include/adi.h): argument marshalling only.
+
+Every step of the ADI path runs inside the library's CUDA kernels.  There is no CPU
+fallback: if the library cannot be loaded (not built, or no CUDA device) the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads
+
+ADI_CFD = 0
+ADI_MFD = 1
+ADI_FP32 = 0
+ADI_FP64 = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libadi.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+_SIGS = {
+    "adi_abi_version": ([], ctypes.c_int),
+    "adi_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "adi_state_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "adi_create": ([ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                    ctypes.c_double, _dp, _dp, _dp, _dp, ctypes.c_int], ctypes.c_int),
+    "adi_set_source": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                        ctypes.c_double], ctypes.c_int),
+    "adi_set_stream": ([_vp, _vp], ctypes.c_int),
+    "adi_step": ([_vp, ctypes.c_int], ctypes.c_int),
+    "adi_sync": ([_vp], ctypes.c_int),
+    "adi_read_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
+    "adi_set_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
+    "adi_check_finite": ([_vp], ctypes.c_int),
+    "adi_get_time": ([_vp, ctypes.POINTER(ctypes.c_longlong), _dp], ctypes.c_int),
+    "adi_destroy": ([_vp], ctypes.c_int),
+    "adi_batch_create": ([ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int], ctypes.c_int),
+    "adi_batch_set_stream": ([_vp, _vp], ctypes.c_int),
+    "adi_batch_step": ([_vp, ctypes.c_int], ctypes.c_int),
+    "adi_batch_sync": ([_vp], ctypes.c_int),
+    "adi_batch_half_step": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "adi_batch_destroy": ([_vp], ctypes.c_int),
+}
+
+
+class AdiError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = lib().adi_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__("%s: %s (code %d)" % (what, msg, code))
+
+
+def lib():
+    """Loads libadi (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libadi.so is missing: the CUDA extension was not built")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise AdiError(rc, what)
+
+
+def _arr(a, shape):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a, a.ctypes.data_as(_dp)
+
+
+def state_bytes(method, nx, ny, precision=ADI_FP32) -> int:
+    return int(lib().adi_state_bytes(method, nx, ny, precision))
+
+
+class Sim:
+    """One simulation resident on the current CUDA device (see adi_create)."""
+
+    def __init__(self, method, nx, ny, h, dt, c, u0=None, v0=None, w0=None,
+                 precision=ADI_FP32):
+        self.method, self.nx, self.ny, self.h, self.dt = method, nx, ny, h, dt
+        self.precision = precision
+        su, sv, sw = workloads.shapes(method, nx, ny)
+        self.shapes = (su, sv, sw)
+        c, cp = _arr(c, su)
+        u0, up = _arr(u0, su)
+        v0, vp = _arr(v0, sv)
+        w0, wp = _arr(w0, sw)
+        h_ = _vp()
+        _check(lib().adi_create(ctypes.byref(h_), method, nx, ny, h, dt, cp, up, vp, wp,
+                                precision), "adi_create")
+        self._h = h_
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_source(self, is_, js, amp, f0, tdelay):
+        _check(lib().adi_set_source(self._h, is_, js, amp, f0, tdelay), "adi_set_source")
+
+    def set_stream(self, stream_ptr):
+        _check(lib().adi_set_stream(self._h, _vp(stream_ptr)), "adi_set_stream")
+
+    def step(self, n=1):
+        _check(lib().adi_step(self._h, int(n)), "adi_step")
+
+    def sync(self):
+        _check(lib().adi_sync(self._h), "adi_sync")
+
+    def read(self):
+        su, sv, sw = self.shapes
+        U, V, W = np.empty(su), np.empty(sv), np.empty(sw)
+        _check(lib().adi_read_fields(self._h, U.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
+                                     W.ctypes.data_as(_dp)), "adi_read_fields")
+        return U, V, W
+
+    def set_fields(self, U=None, V=None, W=None):
+        su, sv, sw = self.shapes
+        U, up = _arr(U, su)
+        V, vp = _arr(V, sv)
+        W, wp = _arr(W, sw)
+        _check(lib().adi_set_fields(self._h, up, vp, wp), "adi_set_fields")
+
+    def read_into(self, U, V, W):
+        """adi_read_fields into caller-provided float64 C-contiguous arrays."""
+        _check(lib().adi_read_fields(self._h, U.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
+                                     W.ctypes.data_as(_dp)), "adi_read_fields")
+
+    def check_finite(self):
+        return lib().adi_check_finite(self._h)
+
+    def time(self):
+        s = ctypes.c_longlong()
+        t = ctypes.c_double()
+        _check(lib().adi_get_time(self._h, ctypes.byref(s), ctypes.byref(t)), "adi_get_time")
+        return s.value, t.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.adi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A group of simulations advanced by one launch per half step (adi_batch_*)."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (_vp * len(self.sims))(*[s.handle for s in self.sims])
+        b = _vp()
+        _check(lib().adi_batch_create(ctypes.byref(b), arr, len(self.sims)), "adi_batch_create")
+        self._b = b
+
+    def set_stream(self, stream_ptr):
+        _check(lib().adi_batch_set_stream(self._b, _vp(stream_ptr)), "adi_batch_set_stream")
+
+    def step(self, n=1):
+        _check(lib().adi_batch_step(self._b, int(n)), "adi_batch_step")
+
+    def sync(self):
+        _check(lib().adi_batch_sync(self._b), "adi_batch_sync")
+
+    def half_step(self, stage, write_natural=False):
+        _check(lib().adi_batch_half_step(self._b, int(stage), 1 if write_natural else 0),
+               "adi_batch_half_step")
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and _lib is not None:
+            _lib.adi_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

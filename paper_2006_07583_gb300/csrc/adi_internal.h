@@ -1,0 +1,52 @@
+// adi_internal.h -- declarations shared by the host side (adi_api.cu) and the kernels
+// (adi_kernels.cu, adi_chunked.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace adi {
+
+// One grid line of one simulation, as every line kernel sees it.  Pressure-like values
+// (a or C, Dirichlet ends included) and alpha share one indexing along the line; the
+// velocity line (v in stage 1, w* in stage 2) has N+1 entries.
+template <typename T>
+struct LineDesc {
+    T *p;              // pressure line, element 0 and element L are the Dirichlet values
+    T *v;              // velocity line v_0..v_N
+    const T *alpha;    // dt/2 * kappa along the pressure line
+    T *u_out;          // natural pressure output (stage-2 lines) or nullptr
+    T *w_out;          // natural velocity output (stage-2 lines) or nullptr
+    const T *tab;      // head/tail elimination tables (kTabLine values)
+    long long sp;      // element stride of p/alpha/u_out along the line
+    long long sv;      // element stride of v/w_out along the line
+    int N;             // cells along the line
+    int method;        // kCFD / kMFD
+    int src_k;         // index along the pressure line of the point source, or -1
+    int advance_clock; // 1: this line's thread advances the simulation clock after use
+    long long *clock;  // completed steps of the owning simulation
+    double beta;       // dt/2 (density 1)
+    double inv_h;
+    double dt;
+    double src_amp, src_f0, src_tdelay; // Ricker source (amp, f0, delay)
+    double src_scale;  // dt / (2 h^2)
+};
+
+// Launchers (defined in adi_kernels.cu).
+template <typename T>
+cudaError_t launch_precompute(const LineDesc<T> *d, int nlines, T *tab_out_base,
+                              int *status, cudaStream_t s);
+template <typename T>
+cudaError_t launch_line_solve_v1(const LineDesc<T> *d, int nlines, T *scratch,
+                                 long long scratch_stride, int write_natural, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prologue(const LineDesc<T> *col_lines, int nlines, const T *u_nat,
+                            const T *w_nat, long long u_ld, long long w_ld, T *scratch,
+                            long long scratch_stride, cudaStream_t s);
+template <typename T>
+cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s);
+
+// Scratch words per line of the thread-per-line solver (solution + block factors).
+size_t v1_scratch_words(int method, int N);
+
+}  // namespace adi

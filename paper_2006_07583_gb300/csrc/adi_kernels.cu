@@ -1,0 +1,623 @@
+// adi_kernels.cu -- line kernels of the Peaceman-Rachford ADI step (arXiv 2006.07583,
+// Sec. 2, Eqs. 6-10 and 12) for sm_103a.
+//
+//   precompute  FP64, once per line: eliminates the one-sided boundary rows of App. A/B
+//               (head and tail of every line system) into small tables.
+//   prologue    turns natural fields (u, v, w) into the carried stage-1 state
+//               a = u - alpha Dbar_y w + dt/2 f and w* = w - beta D_y u (Eq. 8's A and
+//               Alg. 1/2's W*).
+//   line_solve  one half step on a set of lines, thread per line: builds the block
+//               tridiagonal line system on the fly from alpha and the stencils, block
+//               Thomas forward sweep (factors kept in a global scratch), backward sweep,
+//               then the carried outputs C = 2u* - a (+ dt/2 f), v' = 2v* - v.
+//   finite      NaN/Inf scan of a field.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "adi_internal.h"
+#include "adi_ops.cuh"
+
+namespace adi {
+
+// ---------------------------------------------------------------------------------------
+// Small dense helpers.
+// ---------------------------------------------------------------------------------------
+template <typename T, int BS>
+__device__ __forceinline__ void mat_inv(const T (&S)[BS][BS], T (&R)[BS][BS]) {
+    if constexpr (BS == 2) {
+        T det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+        T id = T(1) / det;
+        R[0][0] = S[1][1] * id; R[0][1] = -S[0][1] * id;
+        R[1][0] = -S[1][0] * id; R[1][1] = S[0][0] * id;
+    } else {
+        T c00 = S[1][1] * S[2][2] - S[1][2] * S[2][1];
+        T c01 = S[1][2] * S[2][0] - S[1][0] * S[2][2];
+        T c02 = S[1][0] * S[2][1] - S[1][1] * S[2][0];
+        T det = S[0][0] * c00 + S[0][1] * c01 + S[0][2] * c02;
+        T id = T(1) / det;
+        R[0][0] = c00 * id;
+        R[0][1] = (S[0][2] * S[2][1] - S[0][1] * S[2][2]) * id;
+        R[0][2] = (S[0][1] * S[1][2] - S[0][2] * S[1][1]) * id;
+        R[1][0] = c01 * id;
+        R[1][1] = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) * id;
+        R[1][2] = (S[0][2] * S[1][0] - S[0][0] * S[1][2]) * id;
+        R[2][0] = c02 * id;
+        R[2][1] = (S[0][1] * S[2][0] - S[0][0] * S[2][1]) * id;
+        R[2][2] = (S[0][0] * S[1][1] - S[0][1] * S[1][0]) * id;
+    }
+}
+
+// Ricker wavelet at time t.
+__device__ __forceinline__ double ricker(double amp, double f0, double tdelay, double t) {
+    const double pi = 3.14159265358979323846;
+    double tau = t - tdelay;
+    double q = pi * pi * f0 * f0 * tau * tau;
+    return amp * (1.0 - 2.0 * q) * exp(-q);
+}
+
+// ---------------------------------------------------------------------------------------
+// Line accessors.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Line {
+    const LineDesc<T> &d;
+    __device__ Line(const LineDesc<T> &dd) : d(dd) {}
+    __device__ __forceinline__ T p(int k) const { return d.p[k * d.sp]; }
+    __device__ __forceinline__ T v(int k) const { return d.v[k * d.sv]; }
+    __device__ __forceinline__ T al(int k) const { return d.alpha[k * d.sp]; }
+};
+
+// Pressure-line length minus one (index of the far Dirichlet value).
+__host__ __device__ __forceinline__ int p_last(int method, int N) {
+    return method == kCFD ? N : N + 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Full line system in solver ordering, FP64, for the boundary elimination.
+//   CFD ordering: g_0, e_1, g_1, ..., e_{N-1}, g_{N-1}, g_N  (e_j at 2j-1, g_j at 2j)
+//   MFD ordering: u_1 .. u_N (cell c at c-1)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int cfd_idx_g(int N, int j) { return j == 0 ? 0 : (j == N ? 2 * N - 1 : 2 * j); }
+__device__ __forceinline__ int cfd_idx_e(int j) { return 2 * j - 1; }
+
+template <typename T>
+__device__ double line_entry(const LineDesc<T> &d, int row, int col) {
+    const int N = d.N;
+    const double ih = d.inv_h, beta = d.beta;
+    double w[8];
+    int c0, n;
+    double acc = 0.0;
+    if (d.method == kCFD) {
+        bool is_g = (row == 0) || (row == 2 * N - 1) || (row % 2 == 0);
+        int node = row == 0 ? 0 : (row == 2 * N - 1 ? N : (row + 1) / 2);
+        if (is_g) {
+            n = cfd_P_row(N, node, &c0, w);
+            for (int t = 0; t < n; ++t)
+                if (cfd_idx_g(N, c0 + t) == col) acc += w[t];
+            n = cfd_Q_row(N, node, &c0, w);
+            for (int t = 0; t < n; ++t) {
+                int k = c0 + t;
+                if (k >= 1 && k <= N - 1 && cfd_idx_e(k) == col)
+                    acc += w[t] * ih * (double)d.alpha[k * d.sp];
+            }
+        } else {
+            n = cfd_Pbar_row(N, node, &c0, w);
+            for (int t = 0; t < n; ++t)
+                if (cfd_idx_e(c0 + t) == col) acc += w[t];
+            n = cfd_Qbar_row(N, node, &c0, w);
+            for (int t = 0; t < n; ++t)
+                if (cfd_idx_g(N, c0 + t) == col) acc += w[t] * ih * beta;
+        }
+        return acc;
+    }
+    // MFD Schur row for cell c = row + 1, column cell c' = col + 1.
+    const int c = row + 1, cc = col + 1;
+    double dw[8], gw[8];
+    int d0, g0;
+    int nd = mfd_D_row(N, c - 1, &d0, dw);
+    double s = 0.0;
+    for (int t = 0; t < nd; ++t) {
+        int node = d0 + t;
+        int ng = mfd_G_row(N, node, &g0, gw);
+        int k = cc - g0;
+        if (k >= 0 && k < ng) s += dw[t] * gw[k];
+    }
+    acc = (row == col ? 1.0 : 0.0) - (double)d.alpha[c * d.sp] * beta * ih * ih * s;
+    return acc;
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting of an n x n (n <= 6) matrix.
+__device__ bool small_inverse(double *A, int n, double *R) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) R[i * n + j] = (i == j) ? 1.0 : 0.0;
+    double scale = 0.0;
+    for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(A[i]));
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int i = c + 1; i < n; ++i)
+            if (fabs(A[i * n + c]) > fabs(A[p * n + c])) p = i;
+        if (!(fabs(A[p * n + c]) > 1e-13 * scale)) return false;
+        if (p != c)
+            for (int j = 0; j < n; ++j) {
+                double t = A[c * n + j]; A[c * n + j] = A[p * n + j]; A[p * n + j] = t;
+                t = R[c * n + j]; R[c * n + j] = R[p * n + j]; R[p * n + j] = t;
+            }
+        double ip = 1.0 / A[c * n + c];
+        for (int j = 0; j < n; ++j) { A[c * n + j] *= ip; R[c * n + j] *= ip; }
+        for (int i = 0; i < n; ++i) {
+            if (i == c) continue;
+            double f = A[i * n + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) { A[i * n + j] -= f * A[c * n + j]; R[i * n + j] -= f * R[c * n + j]; }
+        }
+    }
+    return true;
+}
+
+// One thread per line: head and tail elimination tables.
+template <typename T>
+__global__ void precompute_kernel(const LineDesc<T> *__restrict__ descs, int nlines,
+                                  T *tab_out_base, int *status) {
+    int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const LineDesc<T> d = descs[line];
+    const LineShape s = line_shape(d.method, d.N);
+    T *tab = tab_out_base + (size_t)line * kTabLine;
+    const int bs = s.bs;
+    for (int end = 0; end < 2; ++end) {
+        const int m = end == 0 ? s.hu : s.tu;
+        // index ranges: region R (the m eliminated unknowns), adjacent block J (bs)
+        const int r0 = end == 0 ? 0 : s.nunk - s.tu;
+        const int j0 = end == 0 ? s.hu : s.nunk - s.tu - bs;
+        double H[36], Hi[36], E[18], F[18];
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) H[i * m + j] = line_entry(d, r0 + i, r0 + j);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < bs; ++j) E[i * bs + j] = line_entry(d, r0 + i, j0 + j);
+        for (int i = 0; i < bs; ++i)
+            for (int j = 0; j < m; ++j) F[i * m + j] = line_entry(d, j0 + i, r0 + j);
+        if (!small_inverse(H, m, Hi)) { atomicExch(status, 1); return; }
+        T *t = tab + end * kTabEnd;
+        for (int i = 0; i < m * m; ++i) t[kTabHinv + i] = (T)Hi[i];
+        double HiE[18];
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < bs; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < m; ++k) acc += Hi[i * m + k] * E[k * bs + j];
+                HiE[i * bs + j] = acc;
+                t[kTabHinvE + i * bs + j] = (T)acc;
+            }
+        for (int i = 0; i < bs; ++i)
+            for (int j = 0; j < m; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < m; ++k) acc += F[i * m + k] * Hi[k * m + j];
+                t[kTabK + i * m + j] = (T)acc;
+            }
+        for (int i = 0; i < bs; ++i)
+            for (int j = 0; j < bs; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < m; ++k) acc += F[i * m + k] * HiE[k * bs + j];
+                t[kTabDB + i * bs + j] = (T)acc;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Right-hand sides of the head/tail rows (solver index i), in the path's precision.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ T rhs_row(const Line<T> &L, int i) {
+    const LineDesc<T> &d = L.d;
+    const int N = d.N;
+    const T ih = (T)d.inv_h;
+    double w[8];
+    int c0, n;
+    T acc = T(0);
+    if (d.method == kCFD) {
+        bool is_g = (i == 0) || (i == 2 * N - 1) || (i % 2 == 0);
+        int node = i == 0 ? 0 : (i == 2 * N - 1 ? N : (i + 1) / 2);
+        if (is_g) {
+            n = cfd_Q_row(N, node, &c0, w);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * L.p(c0 + t);
+        } else {
+            n = cfd_Qbar_row(N, node, &c0, w);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * L.v(c0 + t);
+        }
+        return acc * ih;
+    }
+    // MFD: r_c = a_c - alpha_c/h * sum_j D[c-1][j] (v_j - beta/h (G[j][0] p_0 + G[j][N+1] p_L))
+    const int c = i + 1;
+    const T p0 = L.p(0), pl = L.p(N + 1), bh = (T)(d.beta * d.inv_h);
+    n = mfd_D_row(N, c - 1, &c0, w);
+    for (int t = 0; t < n; ++t) {
+        int node = c0 + t;
+        T vt = L.v(node);
+        if (node <= 1 || node >= N - 1) {
+            double gw[8];
+            int g0;
+            int ng = mfd_G_row(N, node, &g0, gw);
+            T gb = T(0);
+            if (g0 == 0) gb += (T)gw[0] * p0;
+            if (g0 + ng - 1 == N + 1) gb += (T)gw[ng - 1] * pl;
+            vt -= bh * gb;
+        }
+        acc += (T)w[t] * vt;
+    }
+    return L.p(c) - L.al(c) * ih * acc;
+}
+
+// Middle block b: A (coupling to block b-1), B, C (coupling to block b+1), r.
+template <typename T, int BS>
+__device__ __forceinline__ void middle_block(const Line<T> &L, const LineShape &s, int b,
+                                             T (&A)[BS][BS], T (&B)[BS][BS], T (&C)[BS][BS],
+                                             T (&r)[BS]) {
+    const LineDesc<T> &d = L.d;
+    const T ih = (T)d.inv_h;
+    if constexpr (BS == 2) {
+        const int j = 3 + b;  // node
+        const T tb = T(3) * (T)d.beta * ih;
+        A[0][0] = T(1); A[0][1] = -tb; A[1][0] = -T(3) * ih * L.al(j - 1); A[1][1] = T(1);
+        B[0][0] = T(4); B[0][1] = T(0); B[1][0] = T(0); B[1][1] = T(4);
+        C[0][0] = T(1); C[0][1] = tb; C[1][0] = T(3) * ih * L.al(j + 1); C[1][1] = T(1);
+        r[0] = T(3) * ih * (L.v(j + 1) - L.v(j - 1));
+        r[1] = T(3) * ih * (L.p(j + 1) - L.p(j - 1));
+    } else {
+        const int cb = s.hu + 1 + 3 * b;  // first cell of the block
+        const T w0 = (T)mim_w(0), w1 = (T)mim_w(1), w2 = (T)mim_w(2), w3 = (T)mim_w(3);
+        const T bh2 = (T)(d.beta * d.inv_h * d.inv_h);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int c = cb + k;
+            const T a = L.al(c);
+            const T sc = a * bh2;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                int dA = l - k - 3, dB = l - k, dC = l - k + 3;
+                A[k][l] = (dA >= -3) ? -sc * (T)mim_DG(dA + 3) : T(0);
+                B[k][l] = (dB == 0 ? T(1) : T(0)) - sc * (T)mim_DG(dB + 3);
+                C[k][l] = (dC <= 3) ? -sc * (T)mim_DG(dC + 3) : T(0);
+            }
+            T dv = w0 * L.v(c - 2) + w1 * L.v(c - 1) + w2 * L.v(c) + w3 * L.v(c + 1);
+            r[k] = L.p(c) - a * ih * dv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Thread-per-line solver.
+// ---------------------------------------------------------------------------------------
+size_t v1_scratch_words(int method, int N) {
+    LineShape s = line_shape(method, N);
+    return (size_t)s.nunk + (size_t)s.nb * (s.bs * s.bs + s.bs);
+}
+
+template <typename T, int BS>
+__device__ void solve_line_v1(const LineDesc<T> &d, T *scr, long long st, int write_natural) {
+    const Line<T> L(d);
+    const LineShape s = line_shape(d.method, d.N);
+    const int N = d.N, hu = s.hu, tu = s.tu, nb = s.nb, nunk = s.nunk;
+    auto X = [&](int k) -> T & { return scr[(long long)k * st]; };
+    auto Gm = [&](int b, int i, int j) -> T & { return scr[(long long)(nunk + (b * BS + i) * BS + j) * st]; };
+    auto Y = [&](int b, int i) -> T & { return scr[(long long)(nunk + nb * BS * BS + b * BS + i) * st]; };
+    const T *th = d.tab, *tt = d.tab + kTabEnd;
+
+    T rH[6], rT[6];
+    for (int i = 0; i < hu; ++i) rH[i] = rhs_row(L, i);
+    for (int i = 0; i < tu; ++i) rT[i] = rhs_row(L, nunk - tu + i);
+
+    // forward sweep
+    T Gp[BS][BS], yp[BS];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) { yp[i] = T(0); for (int j = 0; j < BS; ++j) Gp[i][j] = T(0); }
+    for (int b = 0; b < nb; ++b) {
+        T A[BS][BS], B[BS][BS], C[BS][BS], r[BS];
+        middle_block<T, BS>(L, s, b, A, B, C, r);
+        if (b == 0) {
+            for (int i = 0; i < BS; ++i) {
+                for (int j = 0; j < BS; ++j) B[i][j] -= th[kTabDB + i * BS + j];
+                T acc = T(0);
+                for (int k = 0; k < hu; ++k) acc += th[kTabK + i * hu + k] * rH[k];
+                r[i] -= acc;
+            }
+        }
+        if (b == nb - 1) {
+            for (int i = 0; i < BS; ++i) {
+                for (int j = 0; j < BS; ++j) B[i][j] -= tt[kTabDB + i * BS + j];
+                T acc = T(0);
+                for (int k = 0; k < tu; ++k) acc += tt[kTabK + i * tu + k] * rT[k];
+                r[i] -= acc;
+            }
+        }
+        T S[BS][BS], Si[BS][BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+#pragma unroll
+            for (int j = 0; j < BS; ++j) {
+                T acc = B[i][j];
+#pragma unroll
+                for (int k = 0; k < BS; ++k) acc -= A[i][k] * Gp[k][j];
+                S[i][j] = acc;
+            }
+            T acc = r[i];
+#pragma unroll
+            for (int k = 0; k < BS; ++k) acc -= A[i][k] * yp[k];
+            r[i] = acc;
+        }
+        mat_inv<T, BS>(S, Si);
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+#pragma unroll
+            for (int j = 0; j < BS; ++j) {
+                T acc = T(0);
+#pragma unroll
+                for (int k = 0; k < BS; ++k) acc += Si[i][k] * C[k][j];
+                Gp[i][j] = acc;
+                Gm(b, i, j) = acc;
+            }
+        }
+        T yn[BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < BS; ++k) acc += Si[i][k] * r[k];
+            yn[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i) { yp[i] = yn[i]; Y(b, i) = yn[i]; }
+    }
+    // backward sweep: x_b = y_b - Gamma_b x_{b+1}
+    T xn[BS];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) xn[i] = T(0);
+    for (int b = nb - 1; b >= 0; --b) {
+        T x[BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            T acc = Y(b, i);
+#pragma unroll
+            for (int k = 0; k < BS; ++k) acc -= Gm(b, i, k) * xn[k];
+            x[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i) { xn[i] = x[i]; X(hu + b * BS + i) = x[i]; }
+    }
+    // eliminated head/tail unknowns
+    for (int i = 0; i < hu; ++i) {
+        T acc = T(0);
+        for (int k = 0; k < hu; ++k) acc += th[kTabHinv + i * hu + k] * rH[k];
+        for (int k = 0; k < BS; ++k) acc -= th[kTabHinvE + i * BS + k] * X(hu + k);
+        X(i) = acc;
+    }
+    const int lb = hu + (nb - 1) * BS;
+    for (int i = 0; i < tu; ++i) {
+        T acc = T(0);
+        for (int k = 0; k < tu; ++k) acc += tt[kTabHinv + i * tu + k] * rT[k];
+        for (int k = 0; k < BS; ++k) acc -= tt[kTabHinvE + i * BS + k] * X(lb + k);
+        X(nunk - tu + i) = acc;
+    }
+
+    // source term dt/2 f(t_{m+1}) at the source point of this line
+    T src = T(0);
+    if (d.src_k >= 0) {
+        long long m = *d.clock;
+        double t1 = (double)(m + 1) * d.dt;
+        src = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, t1));
+        if (d.advance_clock) *d.clock = m + 1;
+    }
+
+    // epilogue: carried outputs (and natural outputs on request)
+    const T beta = (T)d.beta;
+    if (d.method == kCFD) {
+        for (int j = 0; j <= N; ++j) {
+            T g = X(cfd_idx_g(N, j));
+            T vin = d.v[j * d.sv];
+            d.v[j * d.sv] = vin - T(2) * beta * g;
+            if (write_natural && d.w_out) d.w_out[j * d.sv] = vin - beta * g;
+        }
+        for (int j = 1; j <= N - 1; ++j) {
+            T e = X(cfd_idx_e(j));
+            T pin = d.p[j * d.sp];
+            T ae = L.al(j) * e;
+            d.p[j * d.sp] = pin - T(2) * ae + (j == d.src_k ? src : T(0));
+            if (write_natural && d.u_out) d.u_out[j * d.sp] = pin - ae;
+        }
+    } else {
+        const T ih = (T)d.inv_h;
+        const T p0 = L.p(0), pl = L.p(N + 1);
+        for (int j = 0; j <= N; ++j) {
+            double gw[8];
+            int g0;
+            int ng = mfd_G_row(N, j, &g0, gw);
+            T acc = T(0);
+            for (int t = 0; t < ng; ++t) {
+                int k = g0 + t;  // pressure-line index
+                T uk = (k == 0) ? p0 : (k == N + 1 ? pl : X(k - 1));
+                acc += (T)gw[t] * uk;
+            }
+            T gu = acc * ih;
+            T vin = d.v[j * d.sv];
+            d.v[j * d.sv] = vin - T(2) * beta * gu;
+            if (write_natural && d.w_out) d.w_out[j * d.sv] = vin - beta * gu;
+        }
+        for (int c = 1; c <= N; ++c) {
+            T u = X(c - 1);
+            T pin = d.p[c * d.sp];
+            d.p[c * d.sp] = T(2) * u - pin + (c == d.src_k ? src : T(0));
+            if (write_natural && d.u_out) d.u_out[c * d.sp] = u;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) line_solve_v1_kernel(const LineDesc<T> *__restrict__ descs,
+                                                           int nlines, T *scratch, long long st,
+                                                           int write_natural) {
+    int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const LineDesc<T> d = descs[line];
+    T *scr = scratch + line;
+    if (d.method == kCFD)
+        solve_line_v1<T, 2>(d, scr, st, write_natural);
+    else
+        solve_line_v1<T, 3>(d, scr, st, write_natural);
+}
+
+// ---------------------------------------------------------------------------------------
+// Prologue: carried state from natural fields, one thread per stage-2 (y) line.
+//   a_k  = u_k - alpha_k (Dv w)_k + dt/2 f(t_m)   (interior pressure points)
+//   w*_j = w_j - beta (Du u)_j                      (all velocity points)
+// CFD derivatives solve Pbar e = Qbar w and P g = Q u by the Thomas algorithm.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ void thomas_apply(int N, bool reduced, T *rhs_scr, T *c_scr, long long st) {
+    // Solves (P or Pbar) x = rhs in place; rows indexed 0..n-1 (Pbar row r is node r+1).
+    const int n = reduced ? N - 1 : N + 1;
+    auto R = [&](int k) -> T & { return rhs_scr[(long long)k * st]; };
+    auto Cp = [&](int k) -> T & { return c_scr[(long long)k * st]; };
+    double w[8];
+    int c0;
+    T cprev = T(0), dprev = T(0);
+    for (int r = 0; r < n; ++r) {
+        int len = reduced ? cfd_Pbar_row(N, r + 1, &c0, w) : cfd_P_row(N, r, &c0, w);
+        int first = reduced ? c0 - 1 : c0;  // column index of the first coefficient
+        T lo = T(0), di, up = T(0);
+        if (r == 0) { di = (T)w[0]; up = (T)w[1]; }
+        else if (r == n - 1) { lo = (T)w[0]; di = (T)w[1]; }
+        else { lo = (T)w[0]; di = (T)w[1]; up = (T)w[2]; }
+        (void)first; (void)len;
+        T den = di - lo * cprev;
+        T cn = up / den;
+        T dn = (R(r) - lo * dprev) / den;
+        Cp(r) = cn; R(r) = dn;
+        cprev = cn; dprev = dn;
+    }
+    for (int r = n - 2; r >= 0; --r) R(r) = R(r) - Cp(r) * R(r + 1);
+}
+
+template <typename T>
+__global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nlines, T *scratch,
+                                long long st) {
+    int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const LineDesc<T> d = descs[line];
+    const int N = d.N;
+    const T ih = (T)d.inv_h, beta = (T)d.beta;
+    T *scr = scratch + line;
+    auto S = [&](int k) -> T & { return scr[(long long)k * st]; };
+    const T *un = d.u_out;  // natural u along the line (same indexing as p)
+    const T *wn = d.w_out;  // natural w along the line (same indexing as v)
+    double w[8];
+    int c0;
+    T src = T(0);
+    if (d.src_k >= 0) {
+        double t = (double)(*d.clock) * d.dt;
+        src = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, t));
+    }
+    if (d.method == kCFD) {
+        // g = P^{-1} Q u  (slots 0..N), then w* = w - beta g
+        for (int j = 0; j <= N; ++j) {
+            int n = cfd_Q_row(N, j, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * d.sp];
+            S(j) = acc * ih;
+        }
+        thomas_apply<T>(N, false, scr, scr + (long long)(N + 1) * st, st);
+        for (int j = 0; j <= N; ++j) d.v[j * d.sv] = wn[j * d.sv] - beta * S(j);
+        // e = Pbar^{-1} Qbar w  (slots 0..N-2 for nodes 1..N-1), then a = u - alpha e
+        for (int j = 1; j <= N - 1; ++j) {
+            int n = cfd_Qbar_row(N, j, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * d.sv];
+            S(j - 1) = acc * ih;
+        }
+        thomas_apply<T>(N, true, scr, scr + (long long)(N + 1) * st, st);
+        for (int j = 1; j <= N - 1; ++j) {
+            T val = un[j * d.sp] - d.alpha[j * d.sp] * S(j - 1);
+            if (j == d.src_k) val += src;
+            d.p[j * d.sp] = val;
+        }
+        d.p[0] = un[0];
+        d.p[(long long)N * d.sp] = un[(long long)N * d.sp];
+    } else {
+        for (int j = 0; j <= N; ++j) {
+            int n = mfd_G_row(N, j, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * d.sp];
+            d.v[j * d.sv] = wn[j * d.sv] - beta * acc * ih;
+        }
+        for (int c = 1; c <= N; ++c) {
+            int n = mfd_D_row(N, c - 1, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * d.sv];
+            T val = un[c * d.sp] - d.alpha[c * d.sp] * acc * ih;
+            if (c == d.src_k) val += src;
+            d.p[c * d.sp] = val;
+        }
+        d.p[0] = un[0];
+        d.p[(long long)(N + 1) * d.sp] = un[(long long)(N + 1) * d.sp];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void finite_check_kernel(const T *__restrict__ x, size_t n, int *flag) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < n; i += stride) bad |= !isfinite((double)x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+// ---------------------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_precompute(const LineDesc<T> *d, int nlines, T *tab, int *status,
+                              cudaStream_t s) {
+    if (nlines <= 0) return cudaSuccess;
+    int tpb = 64;
+    precompute_kernel<T><<<(nlines + tpb - 1) / tpb, tpb, 0, s>>>(d, nlines, tab, status);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_line_solve_v1(const LineDesc<T> *d, int nlines, T *scratch, long long st,
+                                 int write_natural, cudaStream_t s) {
+    if (nlines <= 0) return cudaSuccess;
+    int tpb = 128;
+    line_solve_v1_kernel<T><<<(nlines + tpb - 1) / tpb, tpb, 0, s>>>(d, nlines, scratch, st,
+                                                                    write_natural);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_prologue(const LineDesc<T> *d, int nlines, const T *, const T *, long long,
+                            long long, T *scratch, long long st, cudaStream_t s) {
+    if (nlines <= 0) return cudaSuccess;
+    int tpb = 128;
+    prologue_kernel<T><<<(nlines + tpb - 1) / tpb, tpb, 0, s>>>(d, nlines, scratch, st);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    finite_check_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(x, n, flag);
+    return cudaGetLastError();
+}
+
+#define ADI_INST(T)                                                                          \
+    template cudaError_t launch_precompute<T>(const LineDesc<T> *, int, T *, int *,          \
+                                              cudaStream_t);                                 \
+    template cudaError_t launch_line_solve_v1<T>(const LineDesc<T> *, int, T *, long long,   \
+                                                 int, cudaStream_t);                         \
+    template cudaError_t launch_prologue<T>(const LineDesc<T> *, int, const T *, const T *,  \
+                                            long long, long long, T *, long long,            \
+                                            cudaStream_t);                                   \
+    template cudaError_t launch_finite_check<T>(const T *, size_t, int *, cudaStream_t);
+ADI_INST(float)
+ADI_INST(double)
+
+}  // namespace adi
