@@ -364,7 +364,8 @@ def fp64_plain(adi, side):
     specs = make_specs(side, 2)
     tot_pts, tot_s = 0, 0.0
     for sp in specs:
-        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP64)
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP64,
+                    solver=adi.ADI_SOLVER_LINE)
         s.set_source(*sp.source.as_tuple())
         s.step(1)
         s.sync()

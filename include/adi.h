@@ -42,6 +42,10 @@ extern "C" {
 
 typedef enum { ADI_CFD = 0, ADI_MFD = 1 } adi_method;
 typedef enum { ADI_FP32 = 0, ADI_FP64 = 1 } adi_precision;
+/* Line solvers: ADI_SOLVER_LINE runs one thread per grid line (the plain path);
+ * ADI_SOLVER_CHUNKED splits every line into chunks joined by a separator system (the fast
+ * path, the default when a line has at most 256 chunks). */
+typedef enum { ADI_SOLVER_LINE = 0, ADI_SOLVER_CHUNKED = 1 } adi_solver;
 
 typedef enum {
     ADI_OK = 0,
@@ -80,7 +84,16 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
                const double *c_field, const double *u0, const double *v0, const double *w0,
                int precision);
 
-/* Exact device bytes adi_create would allocate for this configuration (0 if invalid). */
+/*
+ * adi_set_solver -- choose the line solver of a handle (adi_solver); rebuilds its per-line
+ * factors.  ADI_ENOTSUP if the chunked solver cannot take lines this long; ADI_EBUSY inside
+ * a batch.  adi_get_solver returns the current one (-1 for a NULL handle).
+ */
+int adi_set_solver(adi_handle sim, int solver);
+int adi_get_solver(adi_handle sim);
+
+/* Device bytes adi_create allocates for this configuration with its default solver (0 if
+ * invalid); transient staging buffers are not included. */
 size_t adi_state_bytes(int method, int nx, int ny, int precision);
 
 /*
@@ -113,7 +126,8 @@ int adi_read_fields(adi_handle sim, double *u, double *v, double *w);
 /*
  * adi_set_fields -- replace the current (U, V, W) by host arrays (shapes above; NULL keeps
  * that field) and rebuild the carried stage-1 state (Eq. 8's A and W* of Alg. 1/2) at the
- * current simulation time.  U's outer rows/columns become the new Dirichlet data.
+ * current simulation time.  U's outer rows/columns become the new Dirichlet data.  Allowed
+ * for a member of a batch (the batch's stream is synchronised first).
  */
 int adi_set_fields(adi_handle sim, const double *u, const double *v, const double *w);
 

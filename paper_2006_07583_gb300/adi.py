@@ -16,6 +16,8 @@ ADI_CFD = 0
 ADI_MFD = 1
 ADI_FP32 = 0
 ADI_FP64 = 1
+ADI_SOLVER_LINE = 0
+ADI_SOLVER_CHUNKED = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libadi.so")
@@ -33,6 +35,8 @@ _SIGS = {
     "adi_set_source": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                         ctypes.c_double], ctypes.c_int),
     "adi_set_stream": ([_vp, _vp], ctypes.c_int),
+    "adi_set_solver": ([_vp, ctypes.c_int], ctypes.c_int),
+    "adi_get_solver": ([_vp], ctypes.c_int),
     "adi_step": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_sync": ([_vp], ctypes.c_int),
     "adi_read_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
@@ -99,7 +103,7 @@ class Sim:
     """One simulation resident on the current CUDA device (see adi_create)."""
 
     def __init__(self, method, nx, ny, h, dt, c, u0=None, v0=None, w0=None,
-                 precision=ADI_FP32):
+                 precision=ADI_FP32, solver=None):
         self.method, self.nx, self.ny, self.h, self.dt = method, nx, ny, h, dt
         self.precision = precision
         su, sv, sw = workloads.shapes(method, nx, ny)
@@ -112,6 +116,8 @@ class Sim:
         _check(lib().adi_create(ctypes.byref(h_), method, nx, ny, h, dt, cp, up, vp, wp,
                                 precision), "adi_create")
         self._h = h_
+        if solver is not None:
+            self.set_solver(solver)
 
     @property
     def handle(self):
@@ -122,6 +128,13 @@ class Sim:
 
     def set_stream(self, stream_ptr):
         _check(lib().adi_set_stream(self._h, _vp(stream_ptr)), "adi_set_stream")
+
+    def set_solver(self, solver):
+        _check(lib().adi_set_solver(self._h, int(solver)), "adi_set_solver")
+
+    @property
+    def solver(self):
+        return lib().adi_get_solver(self._h)
 
     def step(self, n=1):
         _check(lib().adi_step(self._h, int(n)), "adi_step")

@@ -1,15 +1,18 @@
 // adi_api.cu -- host implementation of the C ABI in include/adi.h.
 //
 // Device state of one simulation (precision T):
-//   A      carried pressure, U layout: interior holds a^m (before stage 1) or C (between
-//          the stages); outer rows/columns hold the Dirichlet data.
-//   Vb     v^m (natural), V layout.
-//   Wb     w* (carried), W layout.
+//   A[0]   carried pressure a^m (stage-1 input, stage-2 output), U layout; A[1] holds C
+//          (stage-1 output, stage-2 input).  Outer rows/columns of both hold the Dirichlet data.
+//   V[p]   v^m (natural), V layout; W[p] w* (carried), W layout.  Each half step reads one
+//          copy and writes the other (ping-pong, parity p flips every step), because line
+//          kernels read stencil halos that neighbouring chunks are writing.
 //   alpha  dt/2 * c^2 at U's points.
 //   Uo, Wo natural u, w, written by the last stage-2 launch of every adi_step call.
 //   tab    head/tail elimination tables, one kTabLine record per line (rows then columns).
-//   scratch  per-line scratch of the line solver.
-// One time step = stage-1 launch over the x-lines + stage-2 launch over the y-lines.
+//   sep    separator-system factors of the chunked solver (per line).
+// One time step = stage 1 over the x-lines + stage 2 over the y-lines.  Which kernels run is
+// described by an execution plan (Plan): the thread-per-line solver for some members, the
+// chunked solver (one launch per method) for the others.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,7 +20,6 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <new>
 #include <vector>
 
@@ -33,6 +35,25 @@ struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
 };
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return ADI_OK;
+    if (e == cudaErrorMemoryAllocation) return ADI_ENOMEM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return ADI_ENOTSUP;
+    return ADI_ECUDA;
+}
+
+int dev_alloc(DevBuf &b, size_t bytes) {
+    b.bytes = bytes;
+    if (bytes == 0) { b.p = nullptr; return ADI_OK; }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) { b.p = nullptr; b.bytes = 0; (void)cudaGetLastError(); return cuda_status(e); }
+    return ADI_OK;
+}
+void dev_free(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr; b.bytes = 0;
+}
 
 struct Geometry {
     int method, nx, ny;
@@ -60,6 +81,63 @@ Geometry make_geometry(int method, int nx, int ny) {
 }
 
 size_t elem_size(int precision) { return precision == ADI_FP64 ? 8 : 4; }
+size_t desc_size(int precision) {
+    return precision == ADI_FP64 ? sizeof(LineDesc<double>) : sizeof(LineDesc<float>);
+}
+int block_size(int method) { return method == ADI_CFD ? 2 : 3; }
+
+// Chunked-solver limits: chunks per line must fit one CTA of the kernel.
+constexpr int kChunkThreads = 256;
+
+int chunks_for(int method, int N) { return chunk_count(method, N, chunk_M(method)); }
+
+bool chunked_ok(const Geometry &g) {
+    return chunks_for(g.method, g.nx) <= kChunkThreads && chunks_for(g.method, g.ny) <= kChunkThreads;
+}
+
+size_t sep_words(const Geometry &g) {
+    int bs = block_size(g.method);
+    size_t per = (size_t)3 * bs * bs;
+    return ((size_t)g.piy * (chunks_for(g.method, g.nx) - 1) +
+            (size_t)g.pix * (chunks_for(g.method, g.ny) - 1)) * per;
+}
+
+size_t v1_words(const Geometry &g) {
+    return std::max(v1_scratch_words(g.method, g.nx), v1_scratch_words(g.method, g.ny));
+}
+
+// An execution plan: which kernels advance a set of simulations.
+struct Plan {
+    int precision = ADI_FP32;
+    // thread-per-line members: descriptors per [parity][direction], and their scratch
+    DevBuf v1d[2][2];
+    int v1n[2] = {0, 0};
+    DevBuf scratch;
+    long long scratch_stride = 0;
+    // chunked members: all descriptors per [parity][direction], line groups per [dir][method]
+    DevBuf cd[2][2];
+    DevBuf groups[2][2];
+    int ngroups[2][2] = {{0, 0}, {0, 0}};
+    size_t smem[2][2] = {{0, 0}, {0, 0}};
+    std::map<int, cudaGraphExec_t> graphs;
+};
+
+void drop_graphs(std::map<int, cudaGraphExec_t> &cache) {
+    for (auto &kv : cache) cudaGraphExecDestroy(kv.second);
+    cache.clear();
+}
+
+void plan_free(Plan &p) {
+    drop_graphs(p.graphs);
+    for (int d = 0; d < 2; ++d) {
+        for (int q = 0; q < 2; ++q) { dev_free(p.v1d[q][d]); dev_free(p.cd[q][d]); }
+        for (int m = 0; m < 2; ++m) dev_free(p.groups[d][m]);
+        p.v1n[d] = 0;
+        p.ngroups[d][0] = p.ngroups[d][1] = 0;
+        p.smem[d][0] = p.smem[d][1] = 0;
+    }
+    dev_free(p.scratch);
+}
 
 }  // namespace
 
@@ -68,10 +146,13 @@ struct adi_sim {
     int precision = ADI_FP32;
     double h = 0, dt = 0;
     size_t esz = 4;
-    DevBuf A, Vb, Wb, alpha, Uo, Wo, tab, scratch, rowd, cold, clock, status;
-    long long scratch_stride = 0;
-    int n_row = 0, n_col = 0;
-    std::vector<unsigned char> h_rowd, h_cold;  // host copies of the descriptors
+    DevBuf A[2], V[2], W[2], alpha, Uo, Wo, tab, sep, cold_all, clock, status;
+    int parity = 0;                           // which V/W copy is current
+    int plan_base = 0;                        // parity at which the own plan was built
+    std::vector<unsigned char> h_desc[2][2];  // host descriptors [parity][0 = x-lines, 1 = y-lines]
+    int nlines[2] = {0, 0};
+    int solver = ADI_SOLVER_CHUNKED;
+    Plan plan;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     long long steps = 0;
@@ -81,41 +162,20 @@ struct adi_sim {
     bool src_on = false;
     int src_i = 0, src_j = 0;
     double src_amp = 0, src_f0 = 0, src_td = 0;
-    std::map<int, cudaGraphExec_t> graphs;
 };
 
 struct adi_batch_t {
     std::vector<adi_sim *> sims;
+    std::vector<int> base_parity;  // members' parity when the batch was built
+    int parity = 0;                // batch steps taken, mod 2
     int precision = ADI_FP32;
-    DevBuf rowd, cold, scratch;
-    int n_row = 0, n_col = 0;
-    long long scratch_stride = 0;
+    Plan plan;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int sticky = ADI_OK;
-    std::map<int, cudaGraphExec_t> graphs;
 };
 
 namespace {
-
-int cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return ADI_OK;
-    if (e == cudaErrorMemoryAllocation) return ADI_ENOMEM;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return ADI_ENOTSUP;
-    return ADI_ECUDA;
-}
-
-int dev_alloc(DevBuf &b, size_t bytes) {
-    b.bytes = bytes;
-    if (bytes == 0) { b.p = nullptr; return ADI_OK; }
-    cudaError_t e = cudaMalloc(&b.p, bytes);
-    if (e != cudaSuccess) { b.p = nullptr; (void)cudaGetLastError(); return cuda_status(e); }
-    return ADI_OK;
-}
-void dev_free(DevBuf &b) {
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr; b.bytes = 0;
-}
 
 template <typename T>
 __global__ void convert_from_double(const double *src, T *dst, size_t n, double scale, int square) {
@@ -150,12 +210,19 @@ int upload(adi_sim *s, const double *host, void *dst, size_t n, double *staging,
     return cuda_status(cudaGetLastError());
 }
 
+// Builds the line descriptors of a simulation ([0] x-lines, [1] y-lines).
 template <typename T>
-void fill_descs(adi_sim *s, std::vector<LineDesc<T>> &rows, std::vector<LineDesc<T>> &cols) {
+void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector<LineDesc<T>> &cols) {
     const Geometry &g = s->g;
-    T *A = (T *)s->A.p, *V = (T *)s->Vb.p, *W = (T *)s->Wb.p, *Uo = (T *)s->Uo.p, *Wo = (T *)s->Wo.p;
+    T *A0 = (T *)s->A[0].p, *A1 = (T *)s->A[1].p, *Uo = (T *)s->Uo.p, *Wo = (T *)s->Wo.p;
+    T *Vi = (T *)s->V[par].p, *Vn = (T *)s->V[1 - par].p;
+    T *Wi = (T *)s->W[par].p, *Wn = (T *)s->W[1 - par].p;
     const T *al = (const T *)s->alpha.p;
     const T *tab = (const T *)s->tab.p;
+    T *sep = (T *)s->sep.p;
+    const int bs = block_size(g.method);
+    const int Mx = chunk_M(g.method);
+    const int Tx = chunks_for(g.method, g.nx), Ty = chunks_for(g.method, g.ny);
     LineDesc<T> base;
     std::memset(&base, 0, sizeof(base));
     base.method = g.method;
@@ -166,119 +233,169 @@ void fill_descs(adi_sim *s, std::vector<LineDesc<T>> &rows, std::vector<LineDesc
     base.src_k = -1;
     base.src_amp = s->src_amp; base.src_f0 = s->src_f0; base.src_tdelay = s->src_td;
     base.src_scale = s->dt / (2.0 * s->h * s->h);
+    base.chunkM = Mx;
     rows.assign(g.piy, base);
     cols.assign(g.pix, base);
+    size_t sep_off = 0;
     for (int r = 0; r < g.piy; ++r) {
         int i = r + 1;  // grid row of this x-line
         LineDesc<T> &d = rows[r];
-        d.p = A + (size_t)i * g.ldu;
+        d.p = A0 + (size_t)i * g.ldu;
+        d.po = A1 + (size_t)i * g.ldu;
         d.alpha = al + (size_t)i * g.ldu;
-        d.v = V + (size_t)i * g.ldv;
+        d.v = Vi + (size_t)i * g.ldv;
+        d.vo = Vn + (size_t)i * g.ldv;
         d.u_out = nullptr; d.w_out = nullptr;
         d.sp = 1; d.sv = 1;
         d.N = g.nx;
         d.tab = tab + (size_t)r * kTabLine;
+        d.sep = sep ? sep + sep_off : nullptr;
+        sep_off += (size_t)(Tx - 1) * 3 * bs * bs;
         if (s->src_on && s->src_i == i) d.src_k = s->src_j;
         d.advance_clock = 0;
     }
     for (int c = 0; c < g.pix; ++c) {
         int j = c + 1;  // grid column of this y-line
         LineDesc<T> &d = cols[c];
-        d.p = A + j;
+        d.p = A1 + j;
+        d.po = A0 + j;
         d.alpha = al + j;
-        d.v = W + j;
+        d.v = Wi + j;
+        d.vo = Wn + j;
         d.u_out = Uo + j;
         d.w_out = Wo + j;
         d.sp = g.ldu; d.sv = g.ldw;
         d.N = g.ny;
         d.tab = tab + (size_t)(g.piy + c) * kTabLine;
+        d.sep = sep ? sep + sep_off : nullptr;
+        sep_off += (size_t)(Ty - 1) * 3 * bs * bs;
         if (s->src_on && s->src_j == j) { d.src_k = s->src_i; d.advance_clock = 1; }
     }
 }
 
 template <typename T>
-int upload_descs(adi_sim *s) {
-    std::vector<LineDesc<T>> rows, cols;
-    fill_descs<T>(s, rows, cols);
-    s->h_rowd.assign((unsigned char *)rows.data(), (unsigned char *)(rows.data() + rows.size()));
-    s->h_cold.assign((unsigned char *)cols.data(), (unsigned char *)(cols.data() + cols.size()));
-    cudaError_t e = cudaMemcpyAsync(s->rowd.p, rows.data(), rows.size() * sizeof(LineDesc<T>),
-                                    cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->cold.p, cols.data(), cols.size() * sizeof(LineDesc<T>),
-                            cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return cuda_status(e);
+void build_host_descs(adi_sim *s) {
+    for (int par = 0; par < 2; ++par) {
+        std::vector<LineDesc<T>> rows, cols;
+        fill_descs<T>(s, par, rows, cols);
+        s->h_desc[par][0].assign((unsigned char *)rows.data(), (unsigned char *)(rows.data() + rows.size()));
+        s->h_desc[par][1].assign((unsigned char *)cols.data(), (unsigned char *)(cols.data() + cols.size()));
+    }
 }
 
-size_t scratch_words_for(const Geometry &g) {
-    return std::max(v1_scratch_words(g.method, g.nx), v1_scratch_words(g.method, g.ny));
+// Builds an execution plan for members (all of one precision).  Plan parity q uses each
+// member's descriptors of parity (member's current parity) ^ q.
+int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stream) {
+    plan_free(p);
+    if (members.empty()) return ADI_EINVAL;
+    const int prec = members[0]->precision;
+    p.precision = prec;
+    const size_t dsz = desc_size(prec), esz = elem_size(prec);
+    std::vector<unsigned char> v1[2][2], cd[2][2];
+    std::vector<int4> gr[2][2];
+    size_t words = 0;
+    for (adi_sim *s : members) {
+        for (int dir = 0; dir < 2; ++dir) {
+            if (s->solver == ADI_SOLVER_LINE) {
+                for (int q = 0; q < 2; ++q) {
+                    const std::vector<unsigned char> &h = s->h_desc[s->parity ^ q][dir];
+                    v1[q][dir].insert(v1[q][dir].end(), h.begin(), h.end());
+                }
+            } else {
+                int first = (int)(cd[0][dir].size() / dsz);
+                int n = s->nlines[dir];
+                int N = dir == 0 ? s->g.nx : s->g.ny;
+                int T = chunks_for(s->g.method, N);
+                int nl = std::max(1, kChunkThreads / T);
+                int bs = block_size(s->g.method);
+                for (int st = 0; st < n; st += nl) {
+                    int cnt = std::min(nl, n - st);
+                    gr[dir][s->g.method].push_back(make_int4(first + st, cnt, s->g.method, 0));
+                    size_t sm = (size_t)3 * cnt * T * bs * esz;
+                    p.smem[dir][s->g.method] = std::max(p.smem[dir][s->g.method], sm);
+                }
+                for (int q = 0; q < 2; ++q) {
+                    const std::vector<unsigned char> &h = s->h_desc[s->parity ^ q][dir];
+                    cd[q][dir].insert(cd[q][dir].end(), h.begin(), h.end());
+                }
+            }
+        }
+        if (s->solver == ADI_SOLVER_LINE) words = std::max(words, v1_words(s->g));
+    }
+    int rc = ADI_OK;
+    for (int dir = 0; dir < 2 && !rc; ++dir) {
+        p.v1n[dir] = (int)(v1[0][dir].size() / dsz);
+        for (int q = 0; q < 2 && !rc; ++q) {
+            if (!v1[q][dir].empty()) {
+                rc = dev_alloc(p.v1d[q][dir], v1[q][dir].size());
+                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.v1d[q][dir].p, v1[q][dir].data(), v1[q][dir].size(), cudaMemcpyHostToDevice, stream));
+            }
+            if (!rc && !cd[q][dir].empty()) {
+                rc = dev_alloc(p.cd[q][dir], cd[q][dir].size());
+                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.cd[q][dir].p, cd[q][dir].data(), cd[q][dir].size(), cudaMemcpyHostToDevice, stream));
+            }
+        }
+        for (int m = 0; m < 2 && !rc; ++m) {
+            p.ngroups[dir][m] = (int)gr[dir][m].size();
+            if (!gr[dir][m].empty()) {
+                rc = dev_alloc(p.groups[dir][m], gr[dir][m].size() * sizeof(int4));
+                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.groups[dir][m].p, gr[dir][m].data(), gr[dir][m].size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+            }
+        }
+    }
+    if (!rc && (p.v1n[0] || p.v1n[1])) {
+        p.scratch_stride = std::max(p.v1n[0], p.v1n[1]);
+        rc = dev_alloc(p.scratch, words * (size_t)p.scratch_stride * esz);
+    }
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(stream));
+    if (rc) plan_free(p);
+    return rc;
 }
 
+// One stage (dir 0: stage 1 over x-lines, dir 1: stage 2 over y-lines) of a plan at plan
+// parity q.
 template <typename T>
-int run_prologue(adi_sim *s) {
-    cudaError_t e = launch_prologue<T>((const LineDesc<T> *)s->cold.p, s->n_col, nullptr, nullptr,
-                                       0, 0, (T *)s->scratch.p, s->scratch_stride, s->stream);
-    return cuda_status(e);
+cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream_t stream) {
+    cudaError_t e = cudaSuccess;
+    int nat = dir == 1 ? natural : 0;
+    if (p.v1n[dir])
+        e = launch_line_solve_v1<T>((const LineDesc<T> *)p.v1d[q][dir].p, p.v1n[dir], (T *)p.scratch.p,
+                                    p.scratch_stride, nat, stream);
+    for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+        if (p.ngroups[dir][m])
+            e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
+                                             (const int4 *)p.groups[dir][m].p, p.ngroups[dir][m], m,
+                                             p.smem[dir][m], nat, stream);
+    return e;
 }
 
-int prologue(adi_sim *s) {
-    return s->precision == ADI_FP64 ? run_prologue<double>(s) : run_prologue<float>(s);
+cudaError_t enqueue_stage_any(const Plan &p, int q, int dir, int natural, cudaStream_t stream) {
+    return p.precision == ADI_FP64 ? enqueue_stage<double>(p, q, dir, natural, stream)
+                                   : enqueue_stage<float>(p, q, dir, natural, stream);
 }
 
-template <typename T>
-int run_precompute(adi_sim *s) {
-    cudaError_t e = cudaMemsetAsync(s->status.p, 0, sizeof(int), s->stream);
-    if (e == cudaSuccess)
-        e = launch_precompute<T>((const LineDesc<T> *)s->rowd.p, s->n_row, (T *)s->tab.p,
-                                 (int *)s->status.p, s->stream);
-    if (e == cudaSuccess)
-        e = launch_precompute<T>((const LineDesc<T> *)s->cold.p, s->n_col,
-                                 (T *)s->tab.p + (size_t)s->n_row * kTabLine, (int *)s->status.p,
-                                 s->stream);
-    int st = 0;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&st, s->status.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    return st ? ADI_ESINGULAR : ADI_OK;
-}
-
-// Enqueues one full step (both stages) for a set of row and column descriptors.
-template <typename T>
-cudaError_t enqueue_step(const void *rowd, int n_row, const void *cold, int n_col, void *scratch,
-                         long long st, int natural, cudaStream_t stream) {
-    cudaError_t e = launch_line_solve_v1<T>((const LineDesc<T> *)rowd, n_row, (T *)scratch, st, 0,
-                                            stream);
-    if (e != cudaSuccess) return e;
-    return launch_line_solve_v1<T>((const LineDesc<T> *)cold, n_col, (T *)scratch, st, natural,
-                                   stream);
-}
-
-cudaError_t enqueue_steps(int precision, const void *rowd, int n_row, const void *cold, int n_col,
-                          void *scratch, long long st, int nsteps, cudaStream_t stream) {
+// nsteps full steps starting at plan parity q0.
+cudaError_t enqueue_steps(const Plan &p, int q0, int nsteps, cudaStream_t stream) {
     for (int k = 0; k < nsteps; ++k) {
-        int natural = (k == nsteps - 1) ? 1 : 0;
-        cudaError_t e = precision == ADI_FP64
-                            ? enqueue_step<double>(rowd, n_row, cold, n_col, scratch, st, natural, stream)
-                            : enqueue_step<float>(rowd, n_row, cold, n_col, scratch, st, natural, stream);
+        int q = (q0 + k) & 1;
+        cudaError_t e = enqueue_stage_any(p, q, 0, 0, stream);
+        if (e == cudaSuccess) e = enqueue_stage_any(p, q, 1, k == nsteps - 1 ? 1 : 0, stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// Captures nsteps into a graph (cached per step count) and launches it.
-cudaError_t run_graph(std::map<int, cudaGraphExec_t> &cache, int precision, const void *rowd,
-                      int n_row, const void *cold, int n_col, void *scratch, long long st,
-                      int nsteps, cudaStream_t stream) {
-    auto it = cache.find(nsteps);
-    if (it == cache.end()) {
+// Captures nsteps from parity q0 into a graph (cached per (steps, parity)) and launches it.
+cudaError_t run_graph(Plan &p, int q0, int nsteps, cudaStream_t stream) {
+    const int key = 2 * nsteps + q0;
+    auto it = p.graphs.find(key);
+    if (it == p.graphs.end()) {
         cudaStream_t cap;
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { cudaStreamDestroy(cap); return e; }
-        cudaError_t le = enqueue_steps(precision, rowd, n_row, cold, n_col, scratch, st, nsteps, cap);
+        cudaError_t le = enqueue_steps(p, q0, nsteps, cap);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
@@ -288,14 +405,101 @@ cudaError_t run_graph(std::map<int, cudaGraphExec_t> &cache, int precision, cons
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return e;
-        it = cache.emplace(nsteps, exec).first;
+        it = p.graphs.emplace(key, exec).first;
     }
     return cudaGraphLaunch(it->second, stream);
 }
 
-void drop_graphs(std::map<int, cudaGraphExec_t> &cache) {
-    for (auto &kv : cache) cudaGraphExecDestroy(kv.second);
-    cache.clear();
+// Uploads the sim's descriptors of its current parity (x-lines then y-lines) for the
+// prologue and the precomputes.
+int upload_sim_descs(adi_sim *s) {
+    const std::vector<unsigned char> &hx = s->h_desc[s->parity][0], &hy = s->h_desc[s->parity][1];
+    size_t bytes = hx.size() + hy.size();
+    if (s->cold_all.bytes < bytes) {
+        dev_free(s->cold_all);
+        int rc = dev_alloc(s->cold_all, bytes);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(s->cold_all.p, hx.data(), hx.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((unsigned char *)s->cold_all.p + hx.size(), hy.data(), hy.size(),
+                            cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_status(e);
+}
+
+template <typename T>
+int run_prologue_t(adi_sim *s) {
+    const LineDesc<T> *cols = (const LineDesc<T> *)((unsigned char *)s->cold_all.p + s->h_desc[s->parity][0].size());
+    DevBuf tmp;
+    long long st = std::max(1, s->nlines[1]);
+    int rc = dev_alloc(tmp, (size_t)(2 * s->g.ny + 4) * st * sizeof(T));
+    if (rc) return rc;
+    cudaError_t e = launch_prologue<T>(cols, s->nlines[1], nullptr, nullptr, 0, 0, (T *)tmp.p, st, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    dev_free(tmp);
+    return cuda_status(e);
+}
+
+int prologue(adi_sim *s) {
+    return s->precision == ADI_FP64 ? run_prologue_t<double>(s) : run_prologue_t<float>(s);
+}
+
+template <typename T>
+int run_precompute(adi_sim *s) {
+    const LineDesc<T> *all = (const LineDesc<T> *)s->cold_all.p;
+    int n = s->nlines[0] + s->nlines[1];
+    cudaError_t e = cudaMemsetAsync(s->status.p, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = launch_precompute<T>(all, n, (T *)s->tab.p, (int *)s->status.p, s->stream);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, s->status.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (st) return ADI_ESINGULAR;
+    if (s->solver == ADI_SOLVER_CHUNKED) {
+        e = launch_precompute_sep<T>(all, n, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
+    return cuda_status(e);
+}
+
+// (Re)builds descriptors, separator factors and the plan for the sim's current solver.
+int setup_solver(adi_sim *s) {
+    dev_free(s->sep);
+    int rc = ADI_OK;
+    if (s->solver == ADI_SOLVER_CHUNKED) rc = dev_alloc(s->sep, sep_words(s->g) * s->esz);
+    if (rc) return rc;
+    if (s->precision == ADI_FP64) build_host_descs<double>(s); else build_host_descs<float>(s);
+    rc = upload_sim_descs(s);
+    if (!rc) rc = s->precision == ADI_FP64 ? run_precompute<double>(s) : run_precompute<float>(s);
+    if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
+    s->plan_base = s->parity;
+    return rc;
+}
+
+// Loads natural fields (host; NULL keeps the current natural value) into both ping-pong
+// copies and rebuilds the carried state at the current parity with the prologue (so a
+// member of a batch stays consistent with the batch's plan).
+int load_state(adi_sim *s, const double *u, const double *v, const double *w, bool keep_missing) {
+    const Geometry &g = s->g;
+    const size_t esz = s->esz;
+    DevBuf staging;
+    int rc = dev_alloc(staging, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
+    if (rc) return rc;
+    const int cur = s->parity;
+    if (v || !keep_missing) rc = upload(s, v, s->V[cur].p, g.nV(), (double *)staging.p, 1.0, 0);
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nV() * esz, cudaMemcpyDeviceToDevice, s->stream));
+    if (!rc && (u || !keep_missing)) rc = upload(s, u, s->Uo.p, g.nU(), (double *)staging.p, 1.0, 0);
+    if (!rc && (w || !keep_missing)) rc = upload(s, w, s->Wo.p, g.nW(), (double *)staging.p, 1.0, 0);
+    for (int k = 0; k < 2 && !rc; ++k) {
+        rc = cuda_status(cudaMemcpyAsync(s->A[k].p, s->Uo.p, g.nU() * esz, cudaMemcpyDeviceToDevice, s->stream));
+        if (!rc) rc = cuda_status(cudaMemcpyAsync(s->W[k].p, s->Wo.p, g.nW() * esz, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
+    dev_free(staging);
+    if (!rc) rc = upload_sim_descs(s);  // descriptors of the current parity
+    if (!rc) rc = prologue(s);
+    return rc;
 }
 
 bool finite_positive(const double *x, size_t n) {
@@ -310,8 +514,9 @@ bool all_finite(const double *x, size_t n) {
     return true;
 }
 
-size_t desc_size(int precision) {
-    return precision == ADI_FP64 ? sizeof(LineDesc<double>) : sizeof(LineDesc<float>);
+bool valid_config(int method, int nx, int ny, int precision) {
+    return (method == ADI_CFD || method == ADI_MFD) && nx >= ADI_MIN_CELLS && ny >= ADI_MIN_CELLS &&
+           nx <= ADI_MAX_CELLS && ny <= ADI_MAX_CELLS && (precision == ADI_FP32 || precision == ADI_FP64);
 }
 
 }  // namespace
@@ -336,17 +541,16 @@ const char *adi_strerror(int code) {
 }
 
 size_t adi_state_bytes(int method, int nx, int ny, int precision) {
-    if ((method != ADI_CFD && method != ADI_MFD) || nx < ADI_MIN_CELLS || ny < ADI_MIN_CELLS ||
-        nx > ADI_MAX_CELLS || ny > ADI_MAX_CELLS || (precision != ADI_FP32 && precision != ADI_FP64))
-        return 0;
+    if (!valid_config(method, nx, ny, precision)) return 0;
     Geometry g = make_geometry(method, nx, ny);
     size_t esz = elem_size(precision);
     size_t nl = (size_t)g.pix + g.piy;
     size_t fields = (3 * g.nU() + g.nV() + 2 * g.nW()) * esz;  // A, alpha, Uo, Vb, Wb, Wo
     size_t tab = nl * kTabLine * esz;
-    size_t scratch = scratch_words_for(g) * std::max(g.pix, g.piy) * esz;
-    size_t descs = nl * desc_size(precision);
-    return fields + tab + scratch + descs + 2 * sizeof(long long);
+    size_t descs = 2 * nl * desc_size(precision);  // sim copy + plan copy
+    size_t solver = chunked_ok(g) ? sep_words(g) * esz
+                                  : v1_words(g) * (size_t)std::max(g.pix, g.piy) * esz;
+    return fields + tab + descs + solver + sizeof(long long) + sizeof(int);
 }
 
 int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
@@ -354,9 +558,8 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
                int precision) {
     if (!out) return ADI_EINVAL;
     *out = nullptr;
-    if ((method != ADI_CFD && method != ADI_MFD) || nx < ADI_MIN_CELLS || ny < ADI_MIN_CELLS ||
-        nx > ADI_MAX_CELLS || ny > ADI_MAX_CELLS || (precision != ADI_FP32 && precision != ADI_FP64) ||
-        !(std::isfinite(h) && h > 0) || !(std::isfinite(dt) && dt > 0) || !c_field)
+    if (!valid_config(method, nx, ny, precision) || !(std::isfinite(h) && h > 0) ||
+        !(std::isfinite(dt) && dt > 0) || !c_field)
         return ADI_EINVAL;
     Geometry g = make_geometry(method, nx, ny);
     if (!finite_positive(c_field, g.nU()) || !all_finite(u0, g.nU()) || !all_finite(v0, g.nV()) ||
@@ -368,45 +571,54 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     adi_sim *s = new (std::nothrow) adi_sim;
     if (!s) return ADI_ENOMEM;
     s->g = g; s->precision = precision; s->h = h; s->dt = dt; s->esz = elem_size(precision);
-    s->n_row = g.piy; s->n_col = g.pix;
-    int rc = ADI_OK;
+    s->nlines[0] = g.piy; s->nlines[1] = g.pix;
+    s->solver = chunked_ok(g) ? ADI_SOLVER_CHUNKED : ADI_SOLVER_LINE;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete s; return cuda_status(e); }
     s->own_stream = true;
     const size_t esz = s->esz;
-    s->scratch_stride = std::max(g.pix, g.piy);
-    if (!rc) rc = dev_alloc(s->A, g.nU() * esz);
+    int rc = ADI_OK;
+    for (int k = 0; k < 2 && !rc; ++k) {
+        rc = dev_alloc(s->A[k], g.nU() * esz);
+        if (!rc) rc = dev_alloc(s->V[k], g.nV() * esz);
+        if (!rc) rc = dev_alloc(s->W[k], g.nW() * esz);
+    }
     if (!rc) rc = dev_alloc(s->alpha, g.nU() * esz);
     if (!rc) rc = dev_alloc(s->Uo, g.nU() * esz);
-    if (!rc) rc = dev_alloc(s->Vb, g.nV() * esz);
-    if (!rc) rc = dev_alloc(s->Wb, g.nW() * esz);
     if (!rc) rc = dev_alloc(s->Wo, g.nW() * esz);
     if (!rc) rc = dev_alloc(s->tab, (size_t)(g.pix + g.piy) * kTabLine * esz);
-    if (!rc) rc = dev_alloc(s->scratch, scratch_words_for(g) * (size_t)s->scratch_stride * esz);
-    if (!rc) rc = dev_alloc(s->rowd, (size_t)g.piy * desc_size(precision));
-    if (!rc) rc = dev_alloc(s->cold, (size_t)g.pix * desc_size(precision));
     if (!rc) rc = dev_alloc(s->clock, sizeof(long long));
     if (!rc) rc = dev_alloc(s->status, sizeof(int));
-    DevBuf staging;
-    if (!rc) rc = dev_alloc(staging, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
     if (!rc) rc = cuda_status(cudaMemsetAsync(s->clock.p, 0, sizeof(long long), s->stream));
-    // alpha = dt/2 c^2 ; natural U, W ; v ; the carried buffers get the natural values first
-    if (!rc) rc = upload(s, c_field, s->alpha.p, g.nU(), (double *)staging.p, 0.5 * dt, 1);
-    if (!rc) rc = upload(s, u0, s->Uo.p, g.nU(), (double *)staging.p, 1.0, 0);
-    if (!rc) rc = upload(s, v0, s->Vb.p, g.nV(), (double *)staging.p, 1.0, 0);
-    if (!rc) rc = upload(s, w0, s->Wo.p, g.nW(), (double *)staging.p, 1.0, 0);
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->A.p, s->Uo.p, g.nU() * esz, cudaMemcpyDeviceToDevice, s->stream));
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->Wb.p, s->Wo.p, g.nW() * esz, cudaMemcpyDeviceToDevice, s->stream));
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
-    dev_free(staging);
-    if (!rc) rc = precision == ADI_FP64 ? upload_descs<double>(s) : upload_descs<float>(s);
-    if (!rc) rc = precision == ADI_FP64 ? run_precompute<double>(s) : run_precompute<float>(s);
-    if (!rc) rc = prologue(s);
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
+    if (!rc) {  // alpha = dt/2 c^2
+        DevBuf staging;
+        rc = dev_alloc(staging, g.nU() * sizeof(double));
+        if (!rc) rc = upload(s, c_field, s->alpha.p, g.nU(), (double *)staging.p, 0.5 * dt, 1);
+        if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
+        dev_free(staging);
+    }
+    if (!rc) rc = setup_solver(s);
+    if (!rc) rc = load_state(s, u0, v0, w0, false);
     if (rc) { adi_destroy(s); return rc; }
     *out = s;
     return ADI_OK;
 }
+
+int adi_set_solver(adi_handle s, int solver) {
+    if (!s || (solver != ADI_SOLVER_LINE && solver != ADI_SOLVER_CHUNKED)) return ADI_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (s->in_batch) return ADI_EBUSY;
+    if (solver == ADI_SOLVER_CHUNKED && !chunked_ok(s->g)) return ADI_ENOTSUP;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->sticky = cuda_status(e);
+    if (solver == s->solver) return ADI_OK;
+    s->solver = solver;
+    int rc = setup_solver(s);
+    if (rc) s->sticky = rc;
+    return rc;
+}
+
+int adi_get_solver(adi_handle s) { return s ? s->solver : -1; }
 
 int adi_set_stream(adi_handle s, void *stream) {
     if (!s) return ADI_EINVAL;
@@ -427,9 +639,11 @@ int adi_set_source(adi_handle s, int is, int js, double amp, double f0, double t
     if (e != cudaSuccess) return s->sticky = cuda_status(e);
     s->src_on = true; s->src_i = is; s->src_j = js;
     s->src_amp = amp; s->src_f0 = f0; s->src_td = tdelay;
-    int rc = s->precision == ADI_FP64 ? upload_descs<double>(s) : upload_descs<float>(s);
+    if (s->precision == ADI_FP64) build_host_descs<double>(s); else build_host_descs<float>(s);
+    int rc = upload_sim_descs(s);
+    if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
+    s->plan_base = s->parity;
     if (!rc) rc = prologue(s);  // a picks up dt/2 f(t_now) at the source point
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
     if (rc) s->sticky = rc;
     return rc;
 }
@@ -439,15 +653,13 @@ int adi_step(adi_handle s, int nsteps) {
     if (s->sticky) return s->sticky;
     if (s->in_batch) return ADI_EBUSY;
     if (nsteps == 0) return ADI_OK;
-    cudaError_t e;
-    if (nsteps == 1)
-        e = enqueue_steps(s->precision, s->rowd.p, s->n_row, s->cold.p, s->n_col, s->scratch.p,
-                          s->scratch_stride, 1, s->stream);
-    else
-        e = run_graph(s->graphs, s->precision, s->rowd.p, s->n_row, s->cold.p, s->n_col,
-                      s->scratch.p, s->scratch_stride, nsteps, s->stream);
+    // the own plan's parity 0 is the sim's parity when the plan was built
+    const int q0 = s->parity ^ s->plan_base;
+    cudaError_t e = nsteps == 1 ? enqueue_steps(s->plan, q0, 1, s->stream)
+                                : run_graph(s->plan, q0, nsteps, s->stream);
     if (e != cudaSuccess) return s->sticky = cuda_status(e);
     s->steps += nsteps;
+    s->parity ^= nsteps & 1;
     return ADI_OK;
 }
 
@@ -469,7 +681,7 @@ int adi_read_fields(adi_handle s, double *u, double *v, double *w) {
     if (rc) return rc;
     const Geometry &g = s->g;
     struct { const void *src; double *dst; size_t n; } parts[3] = {
-        {s->Uo.p, u, g.nU()}, {s->Vb.p, v, g.nV()}, {s->Wo.p, w, g.nW()}};
+        {s->Uo.p, u, g.nU()}, {s->V[s->parity].p, v, g.nV()}, {s->Wo.p, w, g.nW()}};
     DevBuf tmp;
     rc = dev_alloc(tmp, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
     if (rc) return rc;
@@ -500,17 +712,7 @@ int adi_set_fields(adi_handle s, const double *u, const double *v, const double 
     if (rc) return rc;
     const Geometry &g = s->g;
     if (!all_finite(u, g.nU()) || !all_finite(v, g.nV()) || !all_finite(w, g.nW())) return ADI_EINVAL;
-    DevBuf staging;
-    rc = dev_alloc(staging, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
-    if (rc) return rc;
-    if (!rc && u) rc = upload(s, u, s->Uo.p, g.nU(), (double *)staging.p, 1.0, 0);
-    if (!rc && u) rc = cuda_status(cudaMemcpyAsync(s->A.p, s->Uo.p, g.nU() * s->esz, cudaMemcpyDeviceToDevice, s->stream));
-    if (!rc && v) rc = upload(s, v, s->Vb.p, g.nV(), (double *)staging.p, 1.0, 0);
-    if (!rc && w) rc = upload(s, w, s->Wo.p, g.nW(), (double *)staging.p, 1.0, 0);
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->Wb.p, s->Wo.p, g.nW() * s->esz, cudaMemcpyDeviceToDevice, s->stream));
-    if (!rc) rc = prologue(s);
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
-    dev_free(staging);
+    rc = load_state(s, u, v, w, true);
     if (rc) s->sticky = rc;
     return rc;
 }
@@ -521,7 +723,7 @@ int adi_check_finite(adi_handle s) {
     if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(s->status.p, 0, sizeof(int), s->stream);
     const Geometry &g = s->g;
-    const void *fields[4] = {s->A.p, s->Vb.p, s->Wb.p, s->Uo.p};
+    const void *fields[4] = {s->A[0].p, s->V[s->parity].p, s->W[s->parity].p, s->Uo.p};
     size_t ns[4] = {g.nU(), g.nV(), g.nW(), g.nU()};
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         e = s->precision == ADI_FP64
@@ -545,9 +747,9 @@ int adi_get_time(adi_handle s, long long *steps, double *t) {
 int adi_destroy(adi_handle s) {
     if (!s) return ADI_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
-    drop_graphs(s->graphs);
-    DevBuf *bufs[] = {&s->A, &s->Vb, &s->Wb, &s->alpha, &s->Uo, &s->Wo, &s->tab, &s->scratch,
-                      &s->rowd, &s->cold, &s->clock, &s->status};
+    plan_free(s->plan);
+    DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
+                      &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status};
     for (DevBuf *b : bufs) dev_free(*b);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     (void)cudaGetLastError();
@@ -556,7 +758,7 @@ int adi_destroy(adi_handle s) {
 }
 
 // ----------------------------------------------------------------------------------------
-// Batches: every member's x-lines in one descriptor table, y-lines in another.
+// Batches: one plan over every member's lines.
 // ----------------------------------------------------------------------------------------
 int adi_batch_create(adi_batch *out, const adi_handle *sims, int n) {
     if (!out || !sims || n < 1) return ADI_EINVAL;
@@ -573,27 +775,13 @@ int adi_batch_create(adi_batch *out, const adi_handle *sims, int n) {
     adi_batch_t *b = new (std::nothrow) adi_batch_t;
     if (!b) return ADI_ENOMEM;
     b->precision = prec;
-    size_t dsz = desc_size(prec), esz = elem_size(prec);
-    std::vector<unsigned char> rows, cols;
-    size_t words = 0;
     for (int k = 0; k < n; ++k) {
-        adi_sim *s = sims[k];
-        cudaStreamSynchronize(s->stream);
-        b->sims.push_back(s);
-        rows.insert(rows.end(), s->h_rowd.begin(), s->h_rowd.end());
-        cols.insert(cols.end(), s->h_cold.begin(), s->h_cold.end());
-        words = std::max(words, scratch_words_for(s->g));
+        cudaStreamSynchronize(sims[k]->stream);
+        b->sims.push_back(sims[k]);
     }
-    b->n_row = (int)(rows.size() / dsz);
-    b->n_col = (int)(cols.size() / dsz);
-    b->scratch_stride = std::max(b->n_row, b->n_col);
     int rc = cuda_status(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     if (!rc) b->own_stream = true;
-    if (!rc) rc = dev_alloc(b->rowd, rows.size());
-    if (!rc) rc = dev_alloc(b->cold, cols.size());
-    if (!rc) rc = dev_alloc(b->scratch, words * (size_t)b->scratch_stride * esz);
-    if (!rc) rc = cuda_status(cudaMemcpy(b->rowd.p, rows.data(), rows.size(), cudaMemcpyHostToDevice));
-    if (!rc) rc = cuda_status(cudaMemcpy(b->cold.p, cols.data(), cols.size(), cudaMemcpyHostToDevice));
+    if (!rc) rc = plan_build(b->plan, b->sims, b->stream);
     if (rc) { adi_batch_destroy(b); return rc; }
     for (adi_sim *s : b->sims) { s->in_batch = true; s->batch_stream = b->stream; }
     *out = b;
@@ -608,41 +796,33 @@ int adi_batch_set_stream(adi_batch b, void *stream) {
     return ADI_OK;
 }
 
+static int batch_fail(adi_batch b, cudaError_t e) {
+    b->sticky = cuda_status(e);
+    for (adi_sim *s : b->sims) s->sticky = b->sticky;
+    return b->sticky;
+}
+
 int adi_batch_step(adi_batch b, int nsteps) {
     if (!b || nsteps < 0) return ADI_EINVAL;
     if (b->sticky) return b->sticky;
     if (nsteps == 0) return ADI_OK;
-    cudaError_t e = run_graph(b->graphs, b->precision, b->rowd.p, b->n_row, b->cold.p, b->n_col,
-                              b->scratch.p, b->scratch_stride, nsteps, b->stream);
-    if (e != cudaSuccess) {
-        b->sticky = cuda_status(e);
-        for (adi_sim *s : b->sims) s->sticky = b->sticky;
-        return b->sticky;
-    }
-    for (adi_sim *s : b->sims) s->steps += nsteps;
+    cudaError_t e = nsteps == 1 ? enqueue_steps(b->plan, b->parity, 1, b->stream)
+                                : run_graph(b->plan, b->parity, nsteps, b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    b->parity ^= nsteps & 1;
+    for (adi_sim *s : b->sims) { s->steps += nsteps; s->parity ^= nsteps & 1; }
     return ADI_OK;
 }
 
 int adi_batch_half_step(adi_batch b, int stage, int write_natural) {
     if (!b || (stage != 1 && stage != 2)) return ADI_EINVAL;
     if (b->sticky) return b->sticky;
-    cudaError_t e;
-    const void *d = stage == 1 ? b->rowd.p : b->cold.p;
-    int n = stage == 1 ? b->n_row : b->n_col;
-    int nat = stage == 2 && write_natural ? 1 : 0;
-    if (b->precision == ADI_FP64)
-        e = launch_line_solve_v1<double>((const LineDesc<double> *)d, n, (double *)b->scratch.p,
-                                         b->scratch_stride, nat, b->stream);
-    else
-        e = launch_line_solve_v1<float>((const LineDesc<float> *)d, n, (float *)b->scratch.p,
-                                        b->scratch_stride, nat, b->stream);
-    if (e != cudaSuccess) {
-        b->sticky = cuda_status(e);
-        for (adi_sim *s : b->sims) s->sticky = b->sticky;
-        return b->sticky;
+    cudaError_t e = enqueue_stage_any(b->plan, b->parity, stage - 1, write_natural ? 1 : 0, b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    if (stage == 2) {
+        b->parity ^= 1;
+        for (adi_sim *s : b->sims) { s->steps += 1; s->parity ^= 1; }
     }
-    if (stage == 2)
-        for (adi_sim *s : b->sims) s->steps += 1;
     return ADI_OK;
 }
 
@@ -650,18 +830,14 @@ int adi_batch_sync(adi_batch b) {
     if (!b) return ADI_EINVAL;
     if (b->sticky) return b->sticky;
     cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) {
-        b->sticky = cuda_status(e);
-        for (adi_sim *s : b->sims) s->sticky = b->sticky;
-    }
-    return b->sticky;
+    if (e != cudaSuccess) return batch_fail(b, e);
+    return ADI_OK;
 }
 
 int adi_batch_destroy(adi_batch b) {
     if (!b) return ADI_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    drop_graphs(b->graphs);
-    dev_free(b->rowd); dev_free(b->cold); dev_free(b->scratch);
+    plan_free(b->plan);
     for (adi_sim *s : b->sims) { s->in_batch = false; s->batch_stream = nullptr; }
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     (void)cudaGetLastError();

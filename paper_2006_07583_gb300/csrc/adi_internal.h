@@ -10,10 +10,14 @@ namespace adi {
 // One grid line of one simulation, as every line kernel sees it.  Pressure-like values
 // (a or C, Dirichlet ends included) and alpha share one indexing along the line; the
 // velocity line (v in stage 1, w* in stage 2) has N+1 entries.
+// Inputs (p, v) and outputs (po, vo) are distinct buffers: line kernels read stencil halos
+// of neighbouring chunks while other chunks write, so a half step never updates in place.
 template <typename T>
 struct LineDesc {
-    T *p;              // pressure line, element 0 and element L are the Dirichlet values
-    T *v;              // velocity line v_0..v_N
+    T *p;              // pressure line (input), element 0 and element L are the Dirichlet values
+    T *v;              // velocity line v_0..v_N (input)
+    T *po;             // pressure line (output, same indexing as p)
+    T *vo;             // velocity line (output, same indexing as v)
     const T *alpha;    // dt/2 * kappa along the pressure line
     T *u_out;          // natural pressure output (stage-2 lines) or nullptr
     T *w_out;          // natural velocity output (stage-2 lines) or nullptr
@@ -30,6 +34,9 @@ struct LineDesc {
     double dt;
     double src_amp, src_f0, src_tdelay; // Ricker source (amp, f0, delay)
     double src_scale;  // dt / (2 h^2)
+    T *sep;            // separator-system factors of the chunked solver (this line)
+    int chunkM;        // chunk length (blocks) the separator factors were built for
+    int pad2;
 };
 
 // Launchers (defined in adi_kernels.cu).
@@ -48,5 +55,15 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
 
 // Scratch words per line of the thread-per-line solver (solution + block factors).
 size_t v1_scratch_words(int method, int N);
+
+// Chunked solver (adi_chunked.cu).
+int chunk_M(int method);                 // chunk length in blocks used by the kernel
+int chunk_count(int method, int N, int M);  // chunks per line
+template <typename T>
+cudaError_t launch_precompute_sep(const LineDesc<T> *d, int nlines, cudaStream_t s);
+template <typename T>
+cudaError_t launch_line_solve_chunked(const LineDesc<T> *d, const int4 *groups, int ngroups,
+                                      int method, size_t smem_bytes, int write_natural,
+                                      cudaStream_t s);
 
 }  // namespace adi

@@ -18,70 +18,15 @@
 
 #include "adi_internal.h"
 #include "adi_ops.cuh"
+#include "adi_line.cuh"
 
 namespace adi {
-
-// ---------------------------------------------------------------------------------------
-// Small dense helpers.
-// ---------------------------------------------------------------------------------------
-template <typename T, int BS>
-__device__ __forceinline__ void mat_inv(const T (&S)[BS][BS], T (&R)[BS][BS]) {
-    if constexpr (BS == 2) {
-        T det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
-        T id = T(1) / det;
-        R[0][0] = S[1][1] * id; R[0][1] = -S[0][1] * id;
-        R[1][0] = -S[1][0] * id; R[1][1] = S[0][0] * id;
-    } else {
-        T c00 = S[1][1] * S[2][2] - S[1][2] * S[2][1];
-        T c01 = S[1][2] * S[2][0] - S[1][0] * S[2][2];
-        T c02 = S[1][0] * S[2][1] - S[1][1] * S[2][0];
-        T det = S[0][0] * c00 + S[0][1] * c01 + S[0][2] * c02;
-        T id = T(1) / det;
-        R[0][0] = c00 * id;
-        R[0][1] = (S[0][2] * S[2][1] - S[0][1] * S[2][2]) * id;
-        R[0][2] = (S[0][1] * S[1][2] - S[0][2] * S[1][1]) * id;
-        R[1][0] = c01 * id;
-        R[1][1] = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) * id;
-        R[1][2] = (S[0][2] * S[1][0] - S[0][0] * S[1][2]) * id;
-        R[2][0] = c02 * id;
-        R[2][1] = (S[0][1] * S[2][0] - S[0][0] * S[2][1]) * id;
-        R[2][2] = (S[0][0] * S[1][1] - S[0][1] * S[1][0]) * id;
-    }
-}
-
-// Ricker wavelet at time t.
-__device__ __forceinline__ double ricker(double amp, double f0, double tdelay, double t) {
-    const double pi = 3.14159265358979323846;
-    double tau = t - tdelay;
-    double q = pi * pi * f0 * f0 * tau * tau;
-    return amp * (1.0 - 2.0 * q) * exp(-q);
-}
-
-// ---------------------------------------------------------------------------------------
-// Line accessors.
-// ---------------------------------------------------------------------------------------
-template <typename T>
-struct Line {
-    const LineDesc<T> &d;
-    __device__ Line(const LineDesc<T> &dd) : d(dd) {}
-    __device__ __forceinline__ T p(int k) const { return d.p[k * d.sp]; }
-    __device__ __forceinline__ T v(int k) const { return d.v[k * d.sv]; }
-    __device__ __forceinline__ T al(int k) const { return d.alpha[k * d.sp]; }
-};
-
-// Pressure-line length minus one (index of the far Dirichlet value).
-__host__ __device__ __forceinline__ int p_last(int method, int N) {
-    return method == kCFD ? N : N + 1;
-}
 
 // ---------------------------------------------------------------------------------------
 // Full line system in solver ordering, FP64, for the boundary elimination.
 //   CFD ordering: g_0, e_1, g_1, ..., e_{N-1}, g_{N-1}, g_N  (e_j at 2j-1, g_j at 2j)
 //   MFD ordering: u_1 .. u_N (cell c at c-1)
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ int cfd_idx_g(int N, int j) { return j == 0 ? 0 : (j == N ? 2 * N - 1 : 2 * j); }
-__device__ __forceinline__ int cfd_idx_e(int j) { return 2 * j - 1; }
-
 template <typename T>
 __device__ double line_entry(const LineDesc<T> &d, int row, int col) {
     const int N = d.N;
@@ -205,87 +150,6 @@ __global__ void precompute_kernel(const LineDesc<T> *__restrict__ descs, int nli
 }
 
 // ---------------------------------------------------------------------------------------
-// Right-hand sides of the head/tail rows (solver index i), in the path's precision.
-// ---------------------------------------------------------------------------------------
-template <typename T>
-__device__ T rhs_row(const Line<T> &L, int i) {
-    const LineDesc<T> &d = L.d;
-    const int N = d.N;
-    const T ih = (T)d.inv_h;
-    double w[8];
-    int c0, n;
-    T acc = T(0);
-    if (d.method == kCFD) {
-        bool is_g = (i == 0) || (i == 2 * N - 1) || (i % 2 == 0);
-        int node = i == 0 ? 0 : (i == 2 * N - 1 ? N : (i + 1) / 2);
-        if (is_g) {
-            n = cfd_Q_row(N, node, &c0, w);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * L.p(c0 + t);
-        } else {
-            n = cfd_Qbar_row(N, node, &c0, w);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * L.v(c0 + t);
-        }
-        return acc * ih;
-    }
-    // MFD: r_c = a_c - alpha_c/h * sum_j D[c-1][j] (v_j - beta/h (G[j][0] p_0 + G[j][N+1] p_L))
-    const int c = i + 1;
-    const T p0 = L.p(0), pl = L.p(N + 1), bh = (T)(d.beta * d.inv_h);
-    n = mfd_D_row(N, c - 1, &c0, w);
-    for (int t = 0; t < n; ++t) {
-        int node = c0 + t;
-        T vt = L.v(node);
-        if (node <= 1 || node >= N - 1) {
-            double gw[8];
-            int g0;
-            int ng = mfd_G_row(N, node, &g0, gw);
-            T gb = T(0);
-            if (g0 == 0) gb += (T)gw[0] * p0;
-            if (g0 + ng - 1 == N + 1) gb += (T)gw[ng - 1] * pl;
-            vt -= bh * gb;
-        }
-        acc += (T)w[t] * vt;
-    }
-    return L.p(c) - L.al(c) * ih * acc;
-}
-
-// Middle block b: A (coupling to block b-1), B, C (coupling to block b+1), r.
-template <typename T, int BS>
-__device__ __forceinline__ void middle_block(const Line<T> &L, const LineShape &s, int b,
-                                             T (&A)[BS][BS], T (&B)[BS][BS], T (&C)[BS][BS],
-                                             T (&r)[BS]) {
-    const LineDesc<T> &d = L.d;
-    const T ih = (T)d.inv_h;
-    if constexpr (BS == 2) {
-        const int j = 3 + b;  // node
-        const T tb = T(3) * (T)d.beta * ih;
-        A[0][0] = T(1); A[0][1] = -tb; A[1][0] = -T(3) * ih * L.al(j - 1); A[1][1] = T(1);
-        B[0][0] = T(4); B[0][1] = T(0); B[1][0] = T(0); B[1][1] = T(4);
-        C[0][0] = T(1); C[0][1] = tb; C[1][0] = T(3) * ih * L.al(j + 1); C[1][1] = T(1);
-        r[0] = T(3) * ih * (L.v(j + 1) - L.v(j - 1));
-        r[1] = T(3) * ih * (L.p(j + 1) - L.p(j - 1));
-    } else {
-        const int cb = s.hu + 1 + 3 * b;  // first cell of the block
-        const T w0 = (T)mim_w(0), w1 = (T)mim_w(1), w2 = (T)mim_w(2), w3 = (T)mim_w(3);
-        const T bh2 = (T)(d.beta * d.inv_h * d.inv_h);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int c = cb + k;
-            const T a = L.al(c);
-            const T sc = a * bh2;
-#pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                int dA = l - k - 3, dB = l - k, dC = l - k + 3;
-                A[k][l] = (dA >= -3) ? -sc * (T)mim_DG(dA + 3) : T(0);
-                B[k][l] = (dB == 0 ? T(1) : T(0)) - sc * (T)mim_DG(dB + 3);
-                C[k][l] = (dC <= 3) ? -sc * (T)mim_DG(dC + 3) : T(0);
-            }
-            T dv = w0 * L.v(c - 2) + w1 * L.v(c - 1) + w2 * L.v(c) + w3 * L.v(c + 1);
-            r[k] = L.p(c) - a * ih * dv;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // Thread-per-line solver.
 // ---------------------------------------------------------------------------------------
 size_t v1_scratch_words(int method, int N) {
@@ -313,7 +177,7 @@ __device__ void solve_line_v1(const LineDesc<T> &d, T *scr, long long st, int wr
     for (int i = 0; i < BS; ++i) { yp[i] = T(0); for (int j = 0; j < BS; ++j) Gp[i][j] = T(0); }
     for (int b = 0; b < nb; ++b) {
         T A[BS][BS], B[BS][BS], C[BS][BS], r[BS];
-        middle_block<T, BS>(L, s, b, A, B, C, r);
+        middle_block<T, T, BS>(L, s, b, A, B, C, r);
         if (b == 0) {
             for (int i = 0; i < BS; ++i) {
                 for (int j = 0; j < BS; ++j) B[i][j] -= th[kTabDB + i * BS + j];
@@ -414,14 +278,14 @@ __device__ void solve_line_v1(const LineDesc<T> &d, T *scr, long long st, int wr
         for (int j = 0; j <= N; ++j) {
             T g = X(cfd_idx_g(N, j));
             T vin = d.v[j * d.sv];
-            d.v[j * d.sv] = vin - T(2) * beta * g;
+            d.vo[j * d.sv] = vin - T(2) * beta * g;
             if (write_natural && d.w_out) d.w_out[j * d.sv] = vin - beta * g;
         }
         for (int j = 1; j <= N - 1; ++j) {
             T e = X(cfd_idx_e(j));
             T pin = d.p[j * d.sp];
             T ae = L.al(j) * e;
-            d.p[j * d.sp] = pin - T(2) * ae + (j == d.src_k ? src : T(0));
+            d.po[j * d.sp] = pin - T(2) * ae + (j == d.src_k ? src : T(0));
             if (write_natural && d.u_out) d.u_out[j * d.sp] = pin - ae;
         }
     } else {
@@ -439,13 +303,13 @@ __device__ void solve_line_v1(const LineDesc<T> &d, T *scr, long long st, int wr
             }
             T gu = acc * ih;
             T vin = d.v[j * d.sv];
-            d.v[j * d.sv] = vin - T(2) * beta * gu;
+            d.vo[j * d.sv] = vin - T(2) * beta * gu;
             if (write_natural && d.w_out) d.w_out[j * d.sv] = vin - beta * gu;
         }
         for (int c = 1; c <= N; ++c) {
             T u = X(c - 1);
             T pin = d.p[c * d.sp];
-            d.p[c * d.sp] = T(2) * u - pin + (c == d.src_k ? src : T(0));
+            d.po[c * d.sp] = T(2) * u - pin + (c == d.src_k ? src : T(0));
             if (write_natural && d.u_out) d.u_out[c * d.sp] = u;
         }
     }
@@ -467,8 +331,9 @@ __global__ void __launch_bounds__(128) line_solve_v1_kernel(const LineDesc<T> *_
 
 // ---------------------------------------------------------------------------------------
 // Prologue: carried state from natural fields, one thread per stage-2 (y) line.
-//   a_k  = u_k - alpha_k (Dv w)_k + dt/2 f(t_m)   (interior pressure points)
-//   w*_j = w_j - beta (Du u)_j                      (all velocity points)
+//   a_k  = u_k - alpha_k (Dv w)_k + dt/2 f(t_m)   (interior pressure points) -> d.po
+//   w*_j = w_j - beta (Du u)_j                      (all velocity points)     -> d.v
+// (d.po of a stage-2 line is the stage-1 input buffer; d.v is the stage-2 input.)
 // CFD derivatives solve Pbar e = Qbar w and P g = Q u by the Thomas algorithm.
 // ---------------------------------------------------------------------------------------
 template <typename T>
@@ -537,10 +402,10 @@ __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nline
         for (int j = 1; j <= N - 1; ++j) {
             T val = un[j * d.sp] - d.alpha[j * d.sp] * S(j - 1);
             if (j == d.src_k) val += src;
-            d.p[j * d.sp] = val;
+            d.po[j * d.sp] = val;
         }
-        d.p[0] = un[0];
-        d.p[(long long)N * d.sp] = un[(long long)N * d.sp];
+        d.po[0] = un[0];
+        d.po[(long long)N * d.sp] = un[(long long)N * d.sp];
     } else {
         for (int j = 0; j <= N; ++j) {
             int n = mfd_G_row(N, j, &c0, w);
@@ -554,10 +419,10 @@ __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nline
             for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * d.sv];
             T val = un[c * d.sp] - d.alpha[c * d.sp] * acc * ih;
             if (c == d.src_k) val += src;
-            d.p[c * d.sp] = val;
+            d.po[c * d.sp] = val;
         }
-        d.p[0] = un[0];
-        d.p[(long long)(N + 1) * d.sp] = un[(long long)(N + 1) * d.sp];
+        d.po[0] = un[0];
+        d.po[(long long)(N + 1) * d.sp] = un[(long long)(N + 1) * d.sp];
     }
 }
 

@@ -58,8 +58,8 @@ def _random_case(method, nx, ny, seed, dirichlet=True):
     return h, dt, c, U, V, W
 
 
-def _run_both(adi, method, nx, ny, h, dt, c, U, V, W, steps, precision, src=None):
-    sim = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=precision)
+def _run_both(adi, method, nx, ny, h, dt, c, U, V, W, steps, precision, src=None, solver=None):
+    sim = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=precision, solver=solver)
     if src is not None:
         sim.set_source(*src)
     sim.step(steps)
@@ -106,20 +106,22 @@ def test_standing_wave_fp32(adi, method):
 SIZES = [(16, 16), (17, 23), (18, 16), (40, 29), (61, 64)]
 
 
+@pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("method", [CFD, MFD])
 @pytest.mark.parametrize("nx,ny", SIZES)
-def test_random_fields_dirichlet_fp64(adi, method, nx, ny):
+def test_random_fields_dirichlet_fp64(adi, method, nx, ny, solver):
     h, dt, c, U, V, W = _random_case(method, nx, ny, seed=nx * 100 + ny + method)
-    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 3, adi.ADI_FP64)
+    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 3, adi.ADI_FP64, solver=solver)
     for g, o in zip(G, O):
         assert _max_rel(g, o) <= 1e-12
 
 
+@pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("method", [CFD, MFD])
 @pytest.mark.parametrize("nx,ny", [(16, 16), (45, 38)])
-def test_random_fields_fp32(adi, method, nx, ny):
+def test_random_fields_fp32(adi, method, nx, ny, solver):
     h, dt, c, U, V, W = _random_case(method, nx, ny, seed=7 + nx + method)
-    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 5, adi.ADI_FP32)
+    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 5, adi.ADI_FP32, solver=solver)
     for g, o in zip(G, O):
         assert _l2_rel(g, o) <= 1e-4
 
@@ -204,3 +206,59 @@ def test_nonfinite_detected(adi):
     s.step(2)
     assert s.check_finite() == 4
     s.close()
+
+
+# multi-chunk lines: CFD chunks of <= 32 node blocks, MFD chunks of <= 16 three-cell blocks;
+# these sizes give several chunks per line with ragged last chunks
+MULTI = [(CFD, 230, 171), (MFD, 260, 197), (CFD, 97, 400), (MFD, 53, 311)]
+
+
+@pytest.mark.parametrize("method,nx,ny", MULTI)
+def test_chunked_multichunk_fp64_vs_oracle(adi, method, nx, ny):
+    h, dt, c, U, V, W = _random_case(method, nx, ny, seed=nx + ny)
+    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 2, adi.ADI_FP64,
+                     solver=adi.ADI_SOLVER_CHUNKED)
+    for g, o in zip(G, O):
+        assert _max_rel(g, o) <= 1e-12
+
+
+@pytest.mark.parametrize("method,nx,ny", MULTI)
+def test_chunked_multichunk_fp32_vs_oracle(adi, method, nx, ny):
+    h, dt, c, U, V, W = _random_case(method, nx, ny, seed=3 * nx + ny)
+    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 4, adi.ADI_FP32,
+                     solver=adi.ADI_SOLVER_CHUNKED)
+    for g, o in zip(G, O):
+        assert _l2_rel(g, o) <= 1e-4
+
+
+@pytest.mark.parametrize("method", [CFD, MFD])
+def test_solvers_agree_seismic_with_source(adi, method):
+    """Thread-per-line and chunked solvers on a layered medium with a Ricker source."""
+    spec = wl.seismic_spec(method, 300, 280, steps=20, h=5.0, seed=9)
+    out = []
+    for solver in (adi.ADI_SOLVER_LINE, adi.ADI_SOLVER_CHUNKED):
+        s = adi.Sim(method, spec.nx, spec.ny, spec.h, spec.dt, spec.c, precision=adi.ADI_FP64,
+                    solver=solver)
+        assert s.solver == solver
+        s.set_source(*spec.source.as_tuple())
+        s.step(20)
+        out.append(s.read())
+        s.close()
+    for a, b in zip(*out):
+        assert _max_rel(a, b) <= 1e-12
+
+
+@pytest.mark.parametrize("method", [CFD, MFD])
+def test_set_fields_restart_matches_continuous_run(adi, method):
+    """Reading the fields, loading them back (adi_set_fields) and continuing equals an
+    uninterrupted FP64 run to rounding (the carried state is rebuilt from the fields)."""
+    nx, ny = 70, 66
+    h, dt, c, U, V, W = _random_case(method, nx, ny, seed=12)
+    a = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=adi.ADI_FP64)
+    b = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=adi.ADI_FP64)
+    a.step(6)
+    b.step(3)
+    b.set_fields(*b.read())
+    b.step(3)
+    for x, y in zip(a.read(), b.read()):
+        assert _max_rel(x, y) <= 1e-12
