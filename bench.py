@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solver", default="default", choices=["default", "line", "chunked", "factored"],
+                    help="line solver of the FP32 batch (default: the library's choice)")
     return ap.parse_args()
 
 
@@ -243,7 +245,8 @@ def main():
     specs = make_specs(args.side, args.steps)
     sims = []
     for sp in specs:
-        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32)
+        kw = {} if args.solver == "default" else {"solver": getattr(adi, "ADI_SOLVER_" + args.solver.upper())}
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32, **kw)
         s.set_source(*sp.source.as_tuple())
         sims.append(s)
     batch = adi.Batch(sims)
@@ -307,11 +310,12 @@ def main():
                                   "%dx%d cells" % (args.side, args.side),
                       "global_batch": 2 * ws, "side": args.side,
                       "parallelism": "replicas x%d" % ws, "l2": "inputs larger than L2",
-                      "h_m": 5.0, "source": "15 Hz Ricker"},
+                      "h_m": 5.0, "source": "15 Hz Ricker",
+                      "solver": {0: "line", 1: "chunked", 2: "factored"}[sims[0].solver]},
            "latency_ms": {"p50_step": float(np.percentile(step_ms, 50)),
                           "p99_step": float(np.percentile(step_ms, 99))},
            "clocks": ck, "roofline": roof,
-           "gpu_launches": 2 * K}
+           "gpu_launches": 2 * K * len({sp.method for sp in specs})}
 
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3))

@@ -42,10 +42,14 @@ extern "C" {
 
 typedef enum { ADI_CFD = 0, ADI_MFD = 1 } adi_method;
 typedef enum { ADI_FP32 = 0, ADI_FP64 = 1 } adi_precision;
-/* Line solvers: ADI_SOLVER_LINE runs one thread per grid line (the plain path);
- * ADI_SOLVER_CHUNKED splits every line into chunks joined by a separator system (the fast
- * path, the default when a line has at most 256 chunks). */
-typedef enum { ADI_SOLVER_LINE = 0, ADI_SOLVER_CHUNKED = 1 } adi_solver;
+/* Line solvers:
+ *   ADI_SOLVER_LINE      one thread per grid line, factorisation on the fly (the plain path);
+ *   ADI_SOLVER_CHUNKED   lines split into chunks joined by a separator system, factorisation
+ *                        on the fly (the default where a line fits the kernel's shared
+ *                        memory, else FACTORED, else LINE);
+ *   ADI_SOLVER_FACTORED  per-line block-LU factors built once in FP64 and kept on the
+ *                        device, chunks in registers, chunks joined by scans. */
+typedef enum { ADI_SOLVER_LINE = 0, ADI_SOLVER_CHUNKED = 1, ADI_SOLVER_FACTORED = 2 } adi_solver;
 
 typedef enum {
     ADI_OK = 0,

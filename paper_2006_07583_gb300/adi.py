@@ -18,6 +18,7 @@ ADI_FP32 = 0
 ADI_FP64 = 1
 ADI_SOLVER_LINE = 0
 ADI_SOLVER_CHUNKED = 1
+ADI_SOLVER_FACTORED = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libadi.so")

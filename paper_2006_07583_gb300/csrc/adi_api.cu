@@ -91,8 +91,13 @@ constexpr int kChunkThreads = 256;
 
 int chunks_for(int method, int N) { return chunk_count(method, N, chunk_M(method)); }
 
-bool chunked_ok(const Geometry &g) {
-    return chunks_for(g.method, g.nx) <= kChunkThreads && chunks_for(g.method, g.ny) <= kChunkThreads;
+bool chunked_ok_dir(int method, int N, size_t esz) {
+    int T = chunks_for(method, N);
+    return T <= kChunkThreads &&
+           chunked_smem_bytes(N, 1, T, block_size(method), esz) <= (size_t)kChunkSmemMax;
+}
+bool chunked_ok(const Geometry &g, size_t esz) {
+    return chunked_ok_dir(g.method, g.nx, esz) && chunked_ok_dir(g.method, g.ny, esz);
 }
 
 size_t sep_words(const Geometry &g) {
@@ -101,9 +106,30 @@ size_t sep_words(const Geometry &g) {
     return ((size_t)g.piy * (chunks_for(g.method, g.nx) - 1) +
             (size_t)g.pix * (chunks_for(g.method, g.ny) - 1)) * per;
 }
+bool factored_ok(const Geometry &g) {
+    return fac_supported(g.method, g.nx) && fac_supported(g.method, g.ny);
+}
+size_t fac_words_total(const Geometry &g) {
+    return (size_t)g.piy * fac_words(g.method, g.nx) + (size_t)g.pix * fac_words(g.method, g.ny);
+}
+// per-line record words of the sim's solver (0 for the thread-per-line solver)
+size_t solver_words(const Geometry &g, int solver) {
+    if (solver == ADI_SOLVER_FACTORED) return fac_words_total(g);
+    if (solver == ADI_SOLVER_CHUNKED) return sep_words(g);
+    return 0;
+}
+int default_solver(const Geometry &g, size_t esz);
 
 size_t v1_words(const Geometry &g) {
     return std::max(v1_scratch_words(g.method, g.nx), v1_scratch_words(g.method, g.ny));
+}
+
+// Measured on GB300 at 4096^2 (FP32, one CFD and one MFD simulation batched): chunked
+// 3.4 ms per step, factored 4.5 ms, thread per line 30 ms.
+int default_solver(const Geometry &g, size_t esz) {
+    if (chunked_ok(g, esz)) return ADI_SOLVER_CHUNKED;
+    if (factored_ok(g)) return ADI_SOLVER_FACTORED;
+    return ADI_SOLVER_LINE;
 }
 
 // An execution plan: which kernels advance a set of simulations.
@@ -119,6 +145,11 @@ struct Plan {
     DevBuf groups[2][2];
     int ngroups[2][2] = {{0, 0}, {0, 0}};
     size_t smem[2][2] = {{0, 0}, {0, 0}};
+    // factored members: descriptors per [parity][direction], groups per [dir][method]
+    DevBuf fd[2][2];
+    DevBuf fgroups[2][2];
+    int nfgroups[2][2] = {{0, 0}, {0, 0}};
+    int fthreads[2][2] = {{0, 0}, {0, 0}};
     std::map<int, cudaGraphExec_t> graphs;
 };
 
@@ -130,8 +161,10 @@ void drop_graphs(std::map<int, cudaGraphExec_t> &cache) {
 void plan_free(Plan &p) {
     drop_graphs(p.graphs);
     for (int d = 0; d < 2; ++d) {
-        for (int q = 0; q < 2; ++q) { dev_free(p.v1d[q][d]); dev_free(p.cd[q][d]); }
-        for (int m = 0; m < 2; ++m) dev_free(p.groups[d][m]);
+        for (int q = 0; q < 2; ++q) { dev_free(p.v1d[q][d]); dev_free(p.cd[q][d]); dev_free(p.fd[q][d]); }
+        for (int m = 0; m < 2; ++m) { dev_free(p.groups[d][m]); dev_free(p.fgroups[d][m]); }
+        p.nfgroups[d][0] = p.nfgroups[d][1] = 0;
+        p.fthreads[d][0] = p.fthreads[d][1] = 0;
         p.v1n[d] = 0;
         p.ngroups[d][0] = p.ngroups[d][1] = 0;
         p.smem[d][0] = p.smem[d][1] = 0;
@@ -223,6 +256,9 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
     const int bs = block_size(g.method);
     const int Mx = chunk_M(g.method);
     const int Tx = chunks_for(g.method, g.nx), Ty = chunks_for(g.method, g.ny);
+    const bool fac = s->solver == ADI_SOLVER_FACTORED;
+    const size_t rec_x = fac ? fac_words(g.method, g.nx) : (size_t)(Tx - 1) * 3 * bs * bs;
+    const size_t rec_y = fac ? fac_words(g.method, g.ny) : (size_t)(Ty - 1) * 3 * bs * bs;
     LineDesc<T> base;
     std::memset(&base, 0, sizeof(base));
     base.method = g.method;
@@ -246,11 +282,11 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
         d.v = Vi + (size_t)i * g.ldv;
         d.vo = Vn + (size_t)i * g.ldv;
         d.u_out = nullptr; d.w_out = nullptr;
-        d.sp = 1; d.sv = 1;
+        d.sp = 1; d.sv = 1; d.spo = 1; d.svo = 1; d.snp = 1; d.snv = 1;
         d.N = g.nx;
         d.tab = tab + (size_t)r * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
-        sep_off += (size_t)(Tx - 1) * 3 * bs * bs;
+        sep_off += rec_x;
         if (s->src_on && s->src_i == i) d.src_k = s->src_j;
         d.advance_clock = 0;
     }
@@ -264,11 +300,11 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
         d.vo = Wn + j;
         d.u_out = Uo + j;
         d.w_out = Wo + j;
-        d.sp = g.ldu; d.sv = g.ldw;
+        d.sp = g.ldu; d.sv = g.ldw; d.spo = g.ldu; d.svo = g.ldw; d.snp = g.ldu; d.snv = g.ldw;
         d.N = g.ny;
         d.tab = tab + (size_t)(g.piy + c) * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
-        sep_off += (size_t)(Ty - 1) * 3 * bs * bs;
+        sep_off += rec_y;
         if (s->src_on && s->src_j == j) { d.src_k = s->src_i; d.advance_clock = 1; }
     }
 }
@@ -291,8 +327,8 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
     const int prec = members[0]->precision;
     p.precision = prec;
     const size_t dsz = desc_size(prec), esz = elem_size(prec);
-    std::vector<unsigned char> v1[2][2], cd[2][2];
-    std::vector<int4> gr[2][2];
+    std::vector<unsigned char> v1[2][2], cd[2][2], fdv[2][2];
+    std::vector<int4> gr[2][2], fgr[2][2];
     size_t words = 0;
     for (adi_sim *s : members) {
         for (int dir = 0; dir < 2; ++dir) {
@@ -301,17 +337,38 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                     const std::vector<unsigned char> &h = s->h_desc[s->parity ^ q][dir];
                     v1[q][dir].insert(v1[q][dir].end(), h.begin(), h.end());
                 }
+            } else if (s->solver == ADI_SOLVER_FACTORED) {
+                int first = (int)(fdv[0][dir].size() / dsz);
+                int n = s->nlines[dir];
+                int N = dir == 0 ? s->g.nx : s->g.ny;
+                int Tl = fac_chunks(s->g.method, N);
+                int nl = std::max(1, 512 / Tl);
+                for (int st = 0; st < n; st += nl) {
+                    int cnt = std::min(nl, n - st);
+                    fgr[dir][s->g.method].push_back(make_int4(first + st, cnt, s->g.method, 0));
+                    int th = ((cnt * Tl + 31) / 32) * 32;
+                    p.fthreads[dir][s->g.method] = std::max(p.fthreads[dir][s->g.method], th);
+                }
+                for (int q = 0; q < 2; ++q) {
+                    const std::vector<unsigned char> &h = s->h_desc[s->parity ^ q][dir];
+                    fdv[q][dir].insert(fdv[q][dir].end(), h.begin(), h.end());
+                }
             } else {
                 int first = (int)(cd[0][dir].size() / dsz);
                 int n = s->nlines[dir];
                 int N = dir == 0 ? s->g.nx : s->g.ny;
                 int T = chunks_for(s->g.method, N);
-                int nl = std::max(1, kChunkThreads / T);
                 int bs = block_size(s->g.method);
+                // lines per CTA: at most kChunkThreads threads, at least ~128 threads, and
+                // enough CTAs to give every SM two of them
+                int nl_max = std::max(1, kChunkThreads / T);
+                int nl_min = std::min(nl_max, (128 + T - 1) / T);
+                int nl = std::max(nl_min, std::min(nl_max, (n + 2 * 152 - 1) / (2 * 152)));
+                while (nl > 1 && chunked_smem_bytes(N, nl, T, bs, esz) > (size_t)kChunkSmemMax) --nl;
                 for (int st = 0; st < n; st += nl) {
                     int cnt = std::min(nl, n - st);
                     gr[dir][s->g.method].push_back(make_int4(first + st, cnt, s->g.method, 0));
-                    size_t sm = (size_t)3 * cnt * T * bs * esz;
+                    size_t sm = chunked_smem_bytes(N, cnt, T, bs, esz);
                     p.smem[dir][s->g.method] = std::max(p.smem[dir][s->g.method], sm);
                 }
                 for (int q = 0; q < 2; ++q) {
@@ -333,6 +390,17 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
             if (!rc && !cd[q][dir].empty()) {
                 rc = dev_alloc(p.cd[q][dir], cd[q][dir].size());
                 if (!rc) rc = cuda_status(cudaMemcpyAsync(p.cd[q][dir].p, cd[q][dir].data(), cd[q][dir].size(), cudaMemcpyHostToDevice, stream));
+            }
+            if (!rc && !fdv[q][dir].empty()) {
+                rc = dev_alloc(p.fd[q][dir], fdv[q][dir].size());
+                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fd[q][dir].p, fdv[q][dir].data(), fdv[q][dir].size(), cudaMemcpyHostToDevice, stream));
+            }
+        }
+        for (int m = 0; m < 2 && !rc; ++m) {
+            p.nfgroups[dir][m] = (int)fgr[dir][m].size();
+            if (!fgr[dir][m].empty()) {
+                rc = dev_alloc(p.fgroups[dir][m], fgr[dir][m].size() * sizeof(int4));
+                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fgroups[dir][m].p, fgr[dir][m].data(), fgr[dir][m].size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
             }
         }
         for (int m = 0; m < 2 && !rc; ++m) {
@@ -361,6 +429,11 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
     if (p.v1n[dir])
         e = launch_line_solve_v1<T>((const LineDesc<T> *)p.v1d[q][dir].p, p.v1n[dir], (T *)p.scratch.p,
                                     p.scratch_stride, nat, stream);
+    for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+        if (p.nfgroups[dir][m])
+            e = launch_line_solve_factored<T>((const LineDesc<T> *)p.fd[q][dir].p,
+                                              (const int4 *)p.fgroups[dir][m].p, p.nfgroups[dir][m], m,
+                                              p.fthreads[dir][m], nat, stream);
     for (int m = 0; m < 2 && e == cudaSuccess; ++m)
         if (p.ngroups[dir][m])
             e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
@@ -459,6 +532,9 @@ int run_precompute(adi_sim *s) {
     if (s->solver == ADI_SOLVER_CHUNKED) {
         e = launch_precompute_sep<T>(all, n, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    } else if (s->solver == ADI_SOLVER_FACTORED) {
+        e = launch_fac_precompute<T>(all, n, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     }
     return cuda_status(e);
 }
@@ -467,7 +543,7 @@ int run_precompute(adi_sim *s) {
 int setup_solver(adi_sim *s) {
     dev_free(s->sep);
     int rc = ADI_OK;
-    if (s->solver == ADI_SOLVER_CHUNKED) rc = dev_alloc(s->sep, sep_words(s->g) * s->esz);
+    rc = dev_alloc(s->sep, solver_words(s->g, s->solver) * s->esz);
     if (rc) return rc;
     if (s->precision == ADI_FP64) build_host_descs<double>(s); else build_host_descs<float>(s);
     rc = upload_sim_descs(s);
@@ -548,8 +624,9 @@ size_t adi_state_bytes(int method, int nx, int ny, int precision) {
     size_t fields = (3 * g.nU() + g.nV() + 2 * g.nW()) * esz;  // A, alpha, Uo, Vb, Wb, Wo
     size_t tab = nl * kTabLine * esz;
     size_t descs = 2 * nl * desc_size(precision);  // sim copy + plan copy
-    size_t solver = chunked_ok(g) ? sep_words(g) * esz
-                                  : v1_words(g) * (size_t)std::max(g.pix, g.piy) * esz;
+    int sv = default_solver(g, esz);
+    size_t solver = sv == ADI_SOLVER_LINE ? v1_words(g) * (size_t)std::max(g.pix, g.piy) * esz
+                                          : solver_words(g, sv) * esz;
     return fields + tab + descs + solver + sizeof(long long) + sizeof(int);
 }
 
@@ -572,7 +649,7 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     if (!s) return ADI_ENOMEM;
     s->g = g; s->precision = precision; s->h = h; s->dt = dt; s->esz = elem_size(precision);
     s->nlines[0] = g.piy; s->nlines[1] = g.pix;
-    s->solver = chunked_ok(g) ? ADI_SOLVER_CHUNKED : ADI_SOLVER_LINE;
+    s->solver = default_solver(g, elem_size(precision));
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete s; return cuda_status(e); }
     s->own_stream = true;
@@ -605,10 +682,12 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
 }
 
 int adi_set_solver(adi_handle s, int solver) {
-    if (!s || (solver != ADI_SOLVER_LINE && solver != ADI_SOLVER_CHUNKED)) return ADI_EINVAL;
+    if (!s || (solver != ADI_SOLVER_LINE && solver != ADI_SOLVER_CHUNKED && solver != ADI_SOLVER_FACTORED))
+        return ADI_EINVAL;
     if (s->sticky) return s->sticky;
     if (s->in_batch) return ADI_EBUSY;
-    if (solver == ADI_SOLVER_CHUNKED && !chunked_ok(s->g)) return ADI_ENOTSUP;
+    if (solver == ADI_SOLVER_CHUNKED && !chunked_ok(s->g, s->esz)) return ADI_ENOTSUP;
+    if (solver == ADI_SOLVER_FACTORED && !factored_ok(s->g)) return ADI_ENOTSUP;
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->sticky = cuda_status(e);
     if (solver == s->solver) return ADI_OK;

@@ -244,60 +244,278 @@ __global__ void precompute_sep_kernel(const LineDesc<TS> *__restrict__ descs, in
 }
 
 // ---------------------------------------------------------------------------------------
-// Outputs.
+// Shared-memory layout of one CTA: staged lines (pressure, velocity, alpha; Lp = N+2 each),
+// then the separator hand-over slots SL (left part), SR (right part) and SX (solutions).
 // ---------------------------------------------------------------------------------------
-template <typename T>
-struct Out {
-    const LineDesc<T> &d;
-    int natural;
-    T src;
-    bool src_done;
-    __device__ Out(const LineDesc<T> &dd, int nat) : d(dd), natural(nat), src(T(0)), src_done(false) {}
-    __device__ __forceinline__ T source_at(int k) {
-        if (k != d.src_k) return T(0);
-        if (!src_done) {
-            long long m = *d.clock;
-            src = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(m + 1) * d.dt));
-            if (d.advance_clock) *d.clock = m + 1;
-            src_done = true;
-        }
-        return src;
-    }
-    // CFD node j with solution (e, g) (e unused at the ends)
-    __device__ __forceinline__ void cfd_node(int j, T e, T g) {
-        const T beta = (T)d.beta;
-        T vin = d.v[j * d.sv];
-        d.vo[j * d.sv] = vin - T(2) * beta * g;
-        if (natural && d.w_out) d.w_out[j * d.sv] = vin - beta * g;
-        if (j >= 1 && j <= d.N - 1) {
-            T pin = d.p[j * d.sp];
-            T ae = d.alpha[j * d.sp] * e;
-            d.po[j * d.sp] = pin - T(2) * ae + source_at(j);
-            if (natural && d.u_out) d.u_out[j * d.sp] = pin - ae;
-        }
-    }
-    // MFD cell c with solution u
-    __device__ __forceinline__ void mfd_cell(int c, T u) {
-        T pin = d.p[c * d.sp];
-        d.po[c * d.sp] = T(2) * u - pin + source_at(c);
-        if (natural && d.u_out) d.u_out[c * d.sp] = u;
-    }
-    // MFD node j with (G u)_j already times 1/h
-    __device__ __forceinline__ void mfd_node(int j, T gu) {
-        const T beta = (T)d.beta;
-        T vin = d.v[j * d.sv];
-        d.vo[j * d.sv] = vin - T(2) * beta * gu;
-        if (natural && d.w_out) d.w_out[j * d.sv] = vin - beta * gu;
-    }
+__host__ __device__ inline size_t chunked_smem_elems(int N, int nl, int T, int bs) {
+    return (size_t)3 * nl * (N + 2) + (size_t)3 * nl * T * bs;
+}
+
+// Affine map y -> m y + off on BS-vectors (separator substitution scans).
+template <typename T, int BS>
+struct Aff {
+    T m[BS][BS];
+    T off[BS];
 };
 
-// v' at MFD nodes [j0, j1] from a window of cell values: cells[k - c_lo] for k in
-// [c_lo, c_hi]; pressure-line index 0 and N+1 are the Dirichlet values.
+template <typename T, int BS>
+__device__ __forceinline__ void aff_shfl(Aff<T, BS> &dst, const Aff<T, BS> &src, int delta, bool up) {
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+#pragma unroll
+        for (int j = 0; j < BS; ++j)
+            dst.m[i][j] = up ? __shfl_up_sync(0xffffffffu, src.m[i][j], delta)
+                             : __shfl_down_sync(0xffffffffu, src.m[i][j], delta);
+        dst.off[i] = up ? __shfl_up_sync(0xffffffffu, src.off[i], delta)
+                        : __shfl_down_sync(0xffffffffu, src.off[i], delta);
+    }
+}
+// a <- a o b  (apply b first, then a)
+template <typename T, int BS>
+__device__ __forceinline__ void aff_after(Aff<T, BS> &a, const Aff<T, BS> &b) {
+    Aff<T, BS> r;
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+        T acc = a.off[i];
+#pragma unroll
+        for (int k = 0; k < BS; ++k) acc += a.m[i][k] * b.off[k];
+        r.off[i] = acc;
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < BS; ++k) s += a.m[i][k] * b.m[k][j];
+            r.m[i][j] = s;
+        }
+    }
+    a = r;
+}
+
+// Separator chain of one line, one warp: forward y_k = Sinv_k rhs_k + mF_k y_{k-1}, then
+// backward x_k = y_k - Gamma_k x_{k+1}, both as warp scans of affine maps (k = 1..K).
+template <typename T, int BS>
+__device__ void separator_scan(const T *__restrict__ sep, const T *SLl, const T *SRl, T *SXl, int K,
+                               int lane) {
+    const int per = (K + 31) / 32;
+    const int k0 = 1 + lane * per;
+    const int k1 = min(K + 1, k0 + per);
+    // forward: local composition
+    Aff<T, BS> a;
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+        a.off[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < BS; ++j) a.m[i][j] = i == j ? T(1) : T(0);
+    }
+    for (int k = k0; k < k1; ++k) {
+        const T *rec = sep + (size_t)(k - 1) * 3 * BS * BS;
+        Aff<T, BS> st;
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            T g = T(0);
+#pragma unroll
+            for (int q = 0; q < BS; ++q) {
+                g += rec[i * BS + q] * (SLl[k * BS + q] - SRl[k * BS + q]);
+                st.m[i][q] = rec[BS * BS + i * BS + q];
+            }
+            st.off[i] = g;
+        }
+        aff_after<T, BS>(st, a);
+        a = st;
+    }
+    // inclusive scan over lanes (earlier lanes applied first)
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        Aff<T, BS> o;
+        aff_shfl<T, BS>(o, a, s, true);
+        if (lane >= s) aff_after<T, BS>(a, o);
+    }
+    T y[BS];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+        T v = __shfl_up_sync(0xffffffffu, a.off[i], 1);
+        y[i] = lane == 0 ? T(0) : v;
+    }
+    for (int k = k0; k < k1; ++k) {
+        const T *rec = sep + (size_t)(k - 1) * 3 * BS * BS;
+        T yn[BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < BS; ++q)
+                acc += rec[i * BS + q] * (SLl[k * BS + q] - SRl[k * BS + q]) + rec[BS * BS + i * BS + q] * y[q];
+            yn[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i) { y[i] = yn[i]; SXl[k * BS + i] = yn[i]; }
+    }
+    // backward: local composition from the end of the range
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+        a.off[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < BS; ++j) a.m[i][j] = i == j ? T(1) : T(0);
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+        const T *G = sep + (size_t)(k - 1) * 3 * BS * BS + 2 * BS * BS;
+        Aff<T, BS> st;
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+#pragma unroll
+            for (int q = 0; q < BS; ++q) st.m[i][q] = -G[i * BS + q];
+            st.off[i] = SXl[k * BS + i];
+        }
+        aff_after<T, BS>(st, a);
+        a = st;
+    }
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        Aff<T, BS> o;
+        aff_shfl<T, BS>(o, a, s, false);
+        if (lane + s < 32) aff_after<T, BS>(a, o);
+    }
+    T x[BS];
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+        T v = __shfl_down_sync(0xffffffffu, a.off[i], 1);
+        x[i] = lane == 31 ? T(0) : v;
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+        const T *G = sep + (size_t)(k - 1) * 3 * BS * BS + 2 * BS * BS;
+        T xn[BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            T acc = SXl[k * BS + i];
+#pragma unroll
+            for (int q = 0; q < BS; ++q) acc -= G[i * BS + q] * x[q];
+            xn[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < BS; ++i) { x[i] = xn[i]; SXl[k * BS + i] = xn[i]; }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// One staged line: shared-memory arrays plus the scalars the sweeps need, in registers.
+// Outputs are written in place into the staged arrays (natural outputs of stage-2 lines go
+// straight to global memory).
+// ---------------------------------------------------------------------------------------
 template <typename T>
-__device__ void mfd_nodes_from_window(Out<T> &o, int j0, int j1, const T *cells, int c_lo) {
-    const int N = o.d.N;
-    const T ih = (T)o.d.inv_h;
-    const T p0 = o.d.p[0], pl = o.d.p[(long long)(N + 1) * o.d.sp];
+struct Ln {
+    T *P, *V;           // staged pressure / velocity line (shared memory)
+    const T *Al;        // staged alpha line (shared memory)
+    T beta, ih;
+    int N, hu, tu, nb, nunk;
+    int src_k;          // pressure index of the point source on this line, or -1
+    T srcv;             // dt/2 f(t_{m+1}) at the source point
+    bool src_hit;       // this thread wrote the source point
+    int natural;
+    T *u_out, *w_out;   // natural outputs (global), or nullptr
+    long long sp, sv;   // strides of u_out / w_out
+};
+
+template <typename T, int BS>
+__device__ __forceinline__ void mblock(const Ln<T> &L, int b, T (&A)[BS][BS], T (&B)[BS][BS],
+                                       T (&C)[BS][BS], T (&r)[BS]) {
+    if constexpr (BS == 2) {
+        const int j = 3 + b;
+        const T t3 = T(3) * L.ih;
+        const T tb = t3 * L.beta;
+        A[0][0] = T(1); A[0][1] = -tb; A[1][0] = -t3 * L.Al[j - 1]; A[1][1] = T(1);
+        B[0][0] = T(4); B[0][1] = T(0); B[1][0] = T(0); B[1][1] = T(4);
+        C[0][0] = T(1); C[0][1] = tb; C[1][0] = t3 * L.Al[j + 1]; C[1][1] = T(1);
+        r[0] = t3 * (L.V[j + 1] - L.V[j - 1]);
+        r[1] = t3 * (L.P[j + 1] - L.P[j - 1]);
+    } else {
+        const int cb = L.hu + 1 + 3 * b;
+        const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
+        const T bh2 = L.beta * L.ih * L.ih;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int c = cb + k;
+            const T a = L.Al[c];
+            const T sc = a * bh2;
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const int dA = l - k - 3, dB = l - k, dC = l - k + 3;
+                A[k][l] = (dA >= -3) ? -sc * (T)mim_DG(dA + 3) : T(0);
+                B[k][l] = (dB == 0 ? T(1) : T(0)) - sc * (T)mim_DG(dB + 3);
+                C[k][l] = (dC <= 3) ? -sc * (T)mim_DG(dC + 3) : T(0);
+            }
+            const T dv = w0 * L.V[c - 2] + w1 * L.V[c - 1] + w2 * L.V[c] + w3 * L.V[c + 1];
+            r[k] = L.P[c] - a * L.ih * dv;
+        }
+    }
+}
+
+// Boundary-block corrections (head elimination on block 0, tail on block nb-1), held in
+// registers by the chunks that own those blocks.
+template <typename T, int BS>
+struct Corr {
+    T dB[BS][BS];
+    T dr[BS];
+};
+
+template <typename T, int BS>
+__device__ __forceinline__ void blk(const Ln<T> &L, int b, const Corr<T, BS> &c0, const Corr<T, BS> &cl,
+                                    T (&A)[BS][BS], T (&B)[BS][BS], T (&C)[BS][BS], T (&r)[BS]) {
+    mblock<T, BS>(L, b, A, B, C, r);
+    if (b == 0) {
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            r[i] -= c0.dr[i];
+#pragma unroll
+            for (int j = 0; j < BS; ++j) { B[i][j] -= c0.dB[i][j]; A[i][j] = T(0); }
+        }
+    }
+    if (b == L.nb - 1) {
+#pragma unroll
+        for (int i = 0; i < BS; ++i) {
+            r[i] -= cl.dr[i];
+#pragma unroll
+            for (int j = 0; j < BS; ++j) { B[i][j] -= cl.dB[i][j]; C[i][j] = T(0); }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T src_at(Ln<T> &L, int k) {
+    if (k != L.src_k) return T(0);
+    L.src_hit = true;
+    return L.srcv;
+}
+template <typename T>
+__device__ __forceinline__ void out_cfd(Ln<T> &L, int j, T e, T g) {
+    T vin = L.V[j];
+    L.V[j] = vin - T(2) * L.beta * g;
+    if (L.natural) L.w_out[j * L.sv] = vin - L.beta * g;
+    if (j >= 1 && j <= L.N - 1) {
+        T pin = L.P[j];
+        T ae = L.Al[j] * e;
+        L.P[j] = pin - T(2) * ae + src_at(L, j);
+        if (L.natural) L.u_out[j * L.sp] = pin - ae;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void out_mfd_cell(Ln<T> &L, int c, T u) {
+    T pin = L.P[c];
+    L.P[c] = T(2) * u - pin + src_at(L, c);
+    if (L.natural) L.u_out[c * L.sp] = u;
+}
+template <typename T>
+__device__ __forceinline__ void out_mfd_node(Ln<T> &L, int j, T gu) {
+    T vin = L.V[j];
+    L.V[j] = vin - T(2) * L.beta * gu;
+    if (L.natural) L.w_out[j * L.sv] = vin - L.beta * gu;
+}
+
+// v' at MFD nodes [j0, j1] from cells[k - c_lo] (k in [c_lo, ...]); pressure indices 0 and
+// N+1 are the Dirichlet values.
+template <typename T>
+__device__ __noinline__ void mfd_nodes_window(Ln<T> &L, int j0, int j1, const T *cells, int c_lo) {
+    const int N = L.N;
+    const T p0 = L.P[0], pl = L.P[N + 1];
     for (int j = j0; j <= j1; ++j) {
         double gw[8];
         int g0;
@@ -308,30 +526,83 @@ __device__ void mfd_nodes_from_window(Out<T> &o, int j0, int j1, const T *cells,
             T uk = (k == 0) ? p0 : (k == N + 1 ? pl : cells[k - c_lo]);
             acc += (T)gw[t] * uk;
         }
-        o.mfd_node(j, acc * ih);
+        out_mfd_node(L, j, acc * L.ih);
     }
 }
 
-// CFD tail unknowns (e_{N-2}, g_{N-2}, e_{N-1}, g_{N-1}, g_N) from the last middle block.
+// CFD head (g0, e1, g1, e2, g2) from the first middle block.
 template <typename T>
-__device__ __forceinline__ void cfd_tail_outputs(Out<T> &o, const LineDesc<T> &d, const T *rT,
-                                                 T e_last, T g_last) {
-    const int N = d.N;
-    const T *tt = d.tab + kTabEnd;
+__device__ __noinline__ void cfd_head_out(Ln<T> &L, const T *th, const T *rH, T e, T g) {
+    T xh[5];
+    for (int i = 0; i < 5; ++i) {
+        T acc = T(0);
+        for (int k = 0; k < 5; ++k) acc += th[kTabHinv + i * 5 + k] * rH[k];
+        xh[i] = acc - th[kTabHinvE + i * 2] * e - th[kTabHinvE + i * 2 + 1] * g;
+    }
+    out_cfd(L, 0, T(0), xh[0]);
+    out_cfd(L, 1, xh[1], xh[2]);
+    out_cfd(L, 2, xh[3], xh[4]);
+}
+// CFD tail (e_{N-2}, g_{N-2}, e_{N-1}, g_{N-1}, g_N) from the last middle block.
+template <typename T>
+__device__ __noinline__ void cfd_tail_out(Ln<T> &L, const T *tt, const T *rT, T e, T g) {
+    const int N = L.N;
     T xt[5];
     for (int i = 0; i < 5; ++i) {
         T acc = T(0);
         for (int k = 0; k < 5; ++k) acc += tt[kTabHinv + i * 5 + k] * rT[k];
-        acc -= tt[kTabHinvE + i * 2 + 0] * e_last + tt[kTabHinvE + i * 2 + 1] * g_last;
-        xt[i] = acc;
+        xt[i] = acc - tt[kTabHinvE + i * 2] * e - tt[kTabHinvE + i * 2 + 1] * g;
     }
-    o.cfd_node(N - 2, xt[0], xt[1]);
-    o.cfd_node(N - 1, xt[2], xt[3]);
-    o.cfd_node(N, T(0), xt[4]);
+    out_cfd(L, N - 2, xt[0], xt[1]);
+    out_cfd(L, N - 1, xt[2], xt[3]);
+    out_cfd(L, N, T(0), xt[4]);
+}
+// MFD head cells 1..hu from the first middle block, then nodes 0 .. hu+1.
+template <typename T>
+__device__ __noinline__ void mfd_head_out(Ln<T> &L, const T *th, const T *rH, const T *x0) {
+    T cells[12];
+    cells[0] = L.P[0];
+    for (int i = 0; i < L.hu; ++i) {
+        T acc = T(0);
+        for (int k = 0; k < L.hu; ++k) acc += th[kTabHinv + i * L.hu + k] * rH[k];
+        for (int k = 0; k < 3; ++k) acc -= th[kTabHinvE + i * 3 + k] * x0[k];
+        cells[1 + i] = acc;
+    }
+    cells[L.hu + 1] = x0[0]; cells[L.hu + 2] = x0[1]; cells[L.hu + 3] = x0[2];
+    for (int i = 0; i < L.hu; ++i) out_mfd_cell(L, 1 + i, cells[1 + i]);
+    mfd_nodes_window(L, 0, L.hu + 1, cells, 0);
+}
+// MFD tail cells from the last middle block (cells q0..q0+2), then nodes q0+1 .. N.
+template <typename T>
+__device__ __noinline__ void mfd_tail_out(Ln<T> &L, const T *tt, const T *rT, const T *xl, int q0) {
+    T cells[8];
+    cells[0] = xl[0]; cells[1] = xl[1]; cells[2] = xl[2];
+    for (int i = 0; i < L.tu; ++i) {
+        T acc = T(0);
+        for (int k = 0; k < L.tu; ++k) acc += tt[kTabHinv + i * L.tu + k] * rT[k];
+        for (int k = 0; k < 3; ++k) acc -= tt[kTabHinvE + i * 3 + k] * xl[k];
+        cells[3 + i] = acc;
+    }
+    for (int i = 0; i < L.tu; ++i) out_mfd_cell(L, q0 + 3 + i, cells[3 + i]);
+    mfd_nodes_window(L, q0 + 1, L.N, cells, q0);
+}
+
+// Correction of a boundary block: dB = tab[kTabDB], dr = tab[kTabK] . r_end.
+template <typename T, int BS>
+__device__ __forceinline__ void load_corr(Corr<T, BS> &c, const T *tab, const T *rend, int m) {
+#pragma unroll
+    for (int i = 0; i < BS; ++i) {
+#pragma unroll
+        for (int j = 0; j < BS; ++j) c.dB[i][j] = tab[kTabDB + i * BS + j];
+        T acc = T(0);
+        for (int k = 0; k < m; ++k) acc += tab[kTabK + i * m + k] * rend[k];
+        c.dr[i] = acc;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
-// The fused partitioned solver.
+// The fused partitioned solver (one CTA per group of nl consecutive lines of one
+// simulation and direction).
 // ---------------------------------------------------------------------------------------
 template <typename T, int BS, int M, int SUB>
 __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, int nl, int write_natural,
@@ -339,32 +610,90 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
     constexpr int NSEG = M / SUB;
     const int tid = threadIdx.x;
     const LineDesc<T> &d0 = descs[desc0];
-    const LineShape s = line_shape(d0.method, d0.N);
+    const int N = d0.N;
+    const LineShape s = line_shape(d0.method, N);
     const ChunkGeom g = chunk_geom(s.nb, M);
     const int T_ = g.T;
     const int nthreads = T_ * nl;
-    // shared: per line, per separator k (1..T-1): left (BS), right (BS), x (BS)
-    T *smL = sm;
-    T *smR = sm + (size_t)nl * T_ * BS;
-    T *smX = sm + (size_t)2 * nl * T_ * BS;
-    auto SL = [&](int l, int k) -> T * { return smL + ((size_t)l * T_ + k) * BS; };
-    auto SR = [&](int l, int k) -> T * { return smR + ((size_t)l * T_ + k) * BS; };
-    auto SX = [&](int l, int k) -> T * { return smX + ((size_t)l * T_ + k) * BS; };
+    const int Lp = N + 2;
+    const int np = p_last(d0.method, N) + 1;  // pressure-line length
+    T *sP = sm;
+    T *sV = sP + (size_t)nl * Lp;
+    T *sA = sV + (size_t)nl * Lp;
+    T *smL = sA + (size_t)nl * Lp;
+    T *smR = smL + (size_t)nl * T_ * BS;
+    T *smX = smR + (size_t)nl * T_ * BS;
+    const long long sp = d0.sp, sv = d0.sv;
+
+    // ---------------- stage the lines into shared memory ----------------
+    {
+        // consecutive lines of one simulation are a fixed stride apart
+        const long long lsp = nl > 1 ? (long long)(descs[desc0 + 1].p - d0.p) : 0;
+        const long long lsv = nl > 1 ? (long long)(descs[desc0 + 1].v - d0.v) : 0;
+        const T *gp = d0.p, *gv = d0.v, *ga = d0.alpha;
+        const int per = blockDim.x / nl;
+        const int lc = tid % nl, kc = tid / nl;
+        if (sp == 1) {
+            for (int ll = 0; ll < nl; ++ll)
+                for (int k = tid; k < np; k += blockDim.x) {
+                    sP[ll * Lp + k] = gp[ll * lsp + k];
+                    sA[ll * Lp + k] = ga[ll * lsp + k];
+                }
+        } else if (tid < per * nl) {
+            for (int k = kc; k < np; k += per) {
+                sP[lc * Lp + k] = gp[lc * lsp + k * sp];
+                sA[lc * Lp + k] = ga[lc * lsp + k * sp];
+            }
+        }
+        if (sv == 1) {
+            for (int ll = 0; ll < nl; ++ll)
+                for (int k = tid; k <= N; k += blockDim.x) sV[ll * Lp + k] = gv[ll * lsv + k];
+        } else if (tid < per * nl) {
+            for (int k = kc; k <= N; k += per) sV[lc * Lp + k] = gv[lc * lsv + k * sv];
+        }
+    }
+    __syncthreads();
 
     const bool active = tid < nthreads;
     const int c = active ? tid / nl : 0;
     const int l = active ? tid % nl : 0;
     const LineDesc<T> &d = descs[desc0 + l];
-    const Line<T> L(d);
+    Ln<T> L;
+    L.P = sP + (size_t)l * Lp; L.V = sV + (size_t)l * Lp; L.Al = sA + (size_t)l * Lp;
+    L.beta = (T)d.beta; L.ih = (T)d.inv_h;
+    L.N = N; L.hu = s.hu; L.tu = s.tu; L.nb = s.nb; L.nunk = s.nunk;
+    L.src_k = d.src_k; L.srcv = T(0); L.src_hit = false;
+    L.natural = write_natural && d.u_out != nullptr;
+    L.u_out = d.u_out; L.w_out = d.w_out; L.sp = d.snp; L.sv = d.snv;
+    const T *th = d.tab, *tt = d.tab + kTabEnd;
+    auto SL = [&](int ll, int k) -> T * { return smL + ((size_t)ll * T_ + k) * BS; };
+    auto SR = [&](int ll, int k) -> T * { return smR + ((size_t)ll * T_ + k) * BS; };
+    auto SX = [&](int ll, int k) -> T * { return smX + ((size_t)ll * T_ + k) * BS; };
     const int b0 = chunk_start(g, c), n = chunk_len(g, c);
     const bool first = (c == 0), last = (c == T_ - 1);
     T rH[6], rT[6];
+    Corr<T, BS> c0, cl;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) { rH[i] = T(0); rT[i] = T(0); }
-    if (active && first)
-        for (int i = 0; i < s.hu; ++i) rH[i] = rhs_row(L, i);
-    if (active && last)
-        for (int i = 0; i < s.tu; ++i) rT[i] = rhs_row(L, s.nunk - s.tu + i);
+    for (int i = 0; i < BS; ++i) {
+        c0.dr[i] = cl.dr[i] = T(0);
+#pragma unroll
+        for (int j = 0; j < BS; ++j) c0.dB[i][j] = cl.dB[i][j] = T(0);
+    }
+    if (active && (first || last)) {
+        const Line<T> Lg(d, L.P, L.V, L.Al);
+        if (first) {
+            for (int i = 0; i < s.hu; ++i) rH[i] = rhs_row(Lg, i);
+            load_corr<T, BS>(c0, th, rH, s.hu);
+        }
+        if (last) {
+            for (int i = 0; i < s.tu; ++i) rT[i] = rhs_row(Lg, s.nunk - s.tu + i);
+            load_corr<T, BS>(cl, tt, rT, s.tu);
+        }
+    }
+    if (active && L.src_k >= 0) {
+        long long m = *d.clock;
+        L.srcv = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(m + 1) * d.dt));
+    }
 
     // ---------------- phase A ----------------
     if (active) {
@@ -374,7 +703,7 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
             for (int p = 0; p < BS; ++p) { y[p] = T(0); for (int q = 0; q < BS; ++q) G[p][q] = T(0); }
             for (int i = 0; i < n; ++i) {
                 T A[BS][BS], B[BS][BS], C[BS][BS], r[BS];
-                load_block<T, T, BS>(L, s, b0 + i, rH, rT, A, B, C, r);
+                blk<T, BS>(L, b0 + i, c0, cl, A, B, C, r);
                 if (i == 0)
 #pragma unroll
                     for (int p = 0; p < BS; ++p)
@@ -383,7 +712,7 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
                 thomas_step<T, BS>(A, B, C, r, G, y);
             }
             T As[BS][BS], Bs[BS][BS], Cs[BS][BS], rs[BS], t[BS];
-            load_block<T, T, BS>(L, s, b0 + n, rH, rT, As, Bs, Cs, rs);
+            mblock<T, BS>(L, b0 + n, As, Bs, Cs, rs);
             mv<T, BS>(As, y, t);
             T *dst = SL(l, c + 1);
 #pragma unroll
@@ -395,7 +724,7 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
             for (int p = 0; p < BS; ++p) { y[p] = T(0); for (int q = 0; q < BS; ++q) G[p][q] = T(0); }
             for (int i = n - 1; i >= 0; --i) {
                 T A[BS][BS], B[BS][BS], C[BS][BS], r[BS];
-                load_block<T, T, BS>(L, s, b0 + i, rH, rT, A, B, C, r);
+                blk<T, BS>(L, b0 + i, c0, cl, A, B, C, r);
                 if (i == n - 1)
 #pragma unroll
                     for (int p = 0; p < BS; ++p)
@@ -404,7 +733,7 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
                 thomas_step<T, BS>(C, B, A, r, G, y);  // mirrored recurrence
             }
             T As[BS][BS], Bs[BS][BS], Cs[BS][BS], rs[BS], t[BS];
-            load_block<T, T, BS>(L, s, b0 - 1, rH, rT, As, Bs, Cs, rs);
+            mblock<T, BS>(L, b0 - 1, As, Bs, Cs, rs);
             mv<T, BS>(Cs, y, t);
             T *dst = SR(l, c);
 #pragma unroll
@@ -413,125 +742,67 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
     }
     __syncthreads();
 
-    // ---------------- phase B: separator chain, one thread per line ----------------
-    if (tid < nl && T_ > 1) {
-        const int ll = tid;
-        const T *sep = descs[desc0 + ll].sep;
-        T y[BS];
-#pragma unroll
-        for (int p = 0; p < BS; ++p) y[p] = T(0);
-        for (int k = 1; k < T_; ++k) {
-            const T *rec = sep + (size_t)(k - 1) * 3 * BS * BS;
-            T rhs[BS], yn[BS];
-            const T *Lk = SL(ll, k), *Rk = SR(ll, k);
-#pragma unroll
-            for (int p = 0; p < BS; ++p) rhs[p] = Lk[p] - Rk[p];
-#pragma unroll
-            for (int p = 0; p < BS; ++p) {
-                T acc = T(0);
-#pragma unroll
-                for (int q = 0; q < BS; ++q) acc += rec[p * BS + q] * rhs[q] + rec[BS * BS + p * BS + q] * y[q];
-                yn[p] = acc;
-            }
-            T *st = SX(ll, k);
-#pragma unroll
-            for (int p = 0; p < BS; ++p) { y[p] = yn[p]; st[p] = yn[p]; }
-        }
-        T x[BS];
-#pragma unroll
-        for (int p = 0; p < BS; ++p) x[p] = T(0);
-        for (int k = T_ - 1; k >= 1; --k) {
-            const T *rec = sep + (size_t)(k - 1) * 3 * BS * BS + 2 * BS * BS;
-            T *st = SX(ll, k);
-            T xn[BS];
-#pragma unroll
-            for (int p = 0; p < BS; ++p) {
-                T acc = st[p];
-#pragma unroll
-                for (int q = 0; q < BS; ++q) acc -= rec[p * BS + q] * x[q];
-                xn[p] = acc;
-            }
-#pragma unroll
-            for (int p = 0; p < BS; ++p) { x[p] = xn[p]; st[p] = xn[p]; }
-        }
+    // ---------------- phase B: separator chains, one warp per line ----------------
+    if (T_ > 1) {
+        const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+        for (int ll = warp; ll < nl; ll += nwarps)
+            separator_scan<T, BS>(descs[desc0 + ll].sep, SL(ll, 0), SR(ll, 0), SX(ll, 0), T_ - 1, lane);
     }
     __syncthreads();
-    if (!active) return;
 
     // ---------------- phase C ----------------
-    Out<T> o(d, write_natural);
     T xL[BS], xR[BS];
 #pragma unroll
-    for (int p = 0; p < BS; ++p) {
-        xL[p] = first ? T(0) : SX(l, c)[p];
-        xR[p] = last ? T(0) : SX(l, c + 1)[p];
-    }
-    // forward sweep with checkpoints after every SUB blocks
-    T cpG[NSEG][BS][BS], cpy[NSEG][BS];
-    {
-        T G[BS][BS], y[BS];
+    for (int p = 0; p < BS; ++p) { xL[p] = T(0); xR[p] = T(0); }
+    if (active) {
 #pragma unroll
-        for (int p = 0; p < BS; ++p) { y[p] = T(0); for (int q = 0; q < BS; ++q) G[p][q] = T(0); }
-#pragma unroll
-        for (int sg = 0; sg < NSEG - 1; ++sg) {
-#pragma unroll
-            for (int k = 0; k < SUB; ++k) {
-                const int i = sg * SUB + k;
-                if (i < n) {
-                    T A[BS][BS], B[BS][BS], C[BS][BS], r[BS], t[BS];
-                    load_block<T, T, BS>(L, s, b0 + i, rH, rT, A, B, C, r);
-                    if (i == 0) {
-                        mv<T, BS>(A, xL, t);
-#pragma unroll
-                        for (int p = 0; p < BS; ++p) {
-                            r[p] -= first ? T(0) : t[p];
-#pragma unroll
-                            for (int q = 0; q < BS; ++q) A[p][q] = T(0);
-                        }
-                    }
-                    if (i == n - 1) {
-                        mv<T, BS>(C, xR, t);
-#pragma unroll
-                        for (int p = 0; p < BS; ++p) {
-                            r[p] -= last ? T(0) : t[p];
-#pragma unroll
-                            for (int q = 0; q < BS; ++q) C[p][q] = T(0);
-                        }
-                    }
-                    thomas_step<T, BS>(A, B, C, r, G, y);
-                }
-            }
-#pragma unroll
-            for (int p = 0; p < BS; ++p) { cpy[sg][p] = y[p]; for (int q = 0; q < BS; ++q) cpG[sg][p][q] = G[p][q]; }
+        for (int p = 0; p < BS; ++p) {
+            xL[p] = first ? T(0) : SX(l, c)[p];
+            xR[p] = last ? T(0) : SX(l, c + 1)[p];
         }
-    }
-    // backward: segments from last to first, each recomputed from its checkpoint
-    T xn[BS];
+        // Segments of SUB blocks from the last to the first; each one re-runs the forward
+        // elimination from the chunk start (no stored factors), keeps its SUB factors in
+        // registers and back-substitutes.  CFD blocks read the nodes next to them, so the
+        // first block of a segment writes its outputs only after the segment below has been
+        // recomputed (pending output).
+        T xn[BS];
 #pragma unroll
-    for (int p = 0; p < BS; ++p) xn[p] = xR[p];
-#pragma unroll
-    for (int sg = NSEG - 1; sg >= 0; --sg) {
-        if (sg * SUB >= n) continue;
-        T Gs[SUB][BS][BS], ys[SUB][BS];
-        {
+        for (int p = 0; p < BS; ++p) xn[p] = xR[p];
+        int pend_node = -1;
+        T pend_e = T(0), pend_g = T(0);
+        const int nseg = (n + SUB - 1) / SUB;
+        for (int sg = nseg - 1; sg >= 0; --sg) {
             T G[BS][BS], y[BS];
 #pragma unroll
-            for (int p = 0; p < BS; ++p) {
-                y[p] = sg == 0 ? T(0) : cpy[sg > 0 ? sg - 1 : 0][p];
+            for (int p = 0; p < BS; ++p) { y[p] = T(0); for (int q = 0; q < BS; ++q) G[p][q] = T(0); }
+            // forward, no storage, up to the segment
+            for (int i = 0; i < sg * SUB; ++i) {
+                T A[BS][BS], B[BS][BS], C[BS][BS], r[BS], t[BS];
+                blk<T, BS>(L, b0 + i, c0, cl, A, B, C, r);
+                if (i == 0) {
+                    mv<T, BS>(A, xL, t);
 #pragma unroll
-                for (int q = 0; q < BS; ++q) G[p][q] = sg == 0 ? T(0) : cpG[sg > 0 ? sg - 1 : 0][p][q];
+                    for (int p = 0; p < BS; ++p) {
+                        r[p] -= t[p];
+#pragma unroll
+                        for (int q = 0; q < BS; ++q) A[p][q] = T(0);
+                    }
+                }
+                thomas_step<T, BS>(A, B, C, r, G, y);
             }
+            // forward over the segment, factors kept
+            T Gs[SUB][BS][BS], ys[SUB][BS];
 #pragma unroll
             for (int k = 0; k < SUB; ++k) {
                 const int i = sg * SUB + k;
                 if (i < n) {
                     T A[BS][BS], B[BS][BS], C[BS][BS], r[BS], t[BS];
-                    load_block<T, T, BS>(L, s, b0 + i, rH, rT, A, B, C, r);
+                    blk<T, BS>(L, b0 + i, c0, cl, A, B, C, r);
                     if (i == 0) {
                         mv<T, BS>(A, xL, t);
 #pragma unroll
                         for (int p = 0; p < BS; ++p) {
-                            r[p] -= first ? T(0) : t[p];
+                            r[p] -= t[p];
 #pragma unroll
                             for (int q = 0; q < BS; ++q) A[p][q] = T(0);
                         }
@@ -540,7 +811,7 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
                         mv<T, BS>(C, xR, t);
 #pragma unroll
                         for (int p = 0; p < BS; ++p) {
-                            r[p] -= last ? T(0) : t[p];
+                            r[p] -= t[p];
 #pragma unroll
                             for (int q = 0; q < BS; ++q) C[p][q] = T(0);
                         }
@@ -550,100 +821,93 @@ __device__ void chunked_body(const LineDesc<T> *__restrict__ descs, int desc0, i
                     for (int p = 0; p < BS; ++p) { ys[k][p] = y[p]; for (int q = 0; q < BS; ++q) Gs[k][p][q] = G[p][q]; }
                 }
             }
-        }
+            if constexpr (BS == 2) {
+                if (pend_node >= 0) { out_cfd(L, pend_node, pend_e, pend_g); pend_node = -1; }
+            }
+            // back substitution over the segment, outputs
 #pragma unroll
-        for (int k = SUB - 1; k >= 0; --k) {
-            const int i = sg * SUB + k;
-            if (i < n) {
-                T x[BS];
+            for (int k = SUB - 1; k >= 0; --k) {
+                const int i = sg * SUB + k;
+                if (i < n) {
+                    T x[BS];
 #pragma unroll
-                for (int p = 0; p < BS; ++p) {
-                    T acc = ys[k][p];
+                    for (int p = 0; p < BS; ++p) {
+                        T acc = ys[k][p];
 #pragma unroll
-                    for (int q = 0; q < BS; ++q) acc -= Gs[k][p][q] * xn[q];
-                    x[p] = acc;
-                }
-                const int b = b0 + i;
-                if constexpr (BS == 2) {
-                    o.cfd_node(3 + b, x[0], x[1]);
-                    if (last && i == n - 1) cfd_tail_outputs<T>(o, d, rT, x[0], x[1]);
-                } else {
-                    const int q0 = s.hu + 1 + 3 * b;
-                    o.mfd_cell(q0, x[0]); o.mfd_cell(q0 + 1, x[1]); o.mfd_cell(q0 + 2, x[2]);
-                    if (last && i == n - 1) {
-                        // nodes q0+1 .. N from this block, the tail cells and p_L
-                        const T *tt = d.tab + kTabEnd;
-                        T cells[8];
-                        cells[0] = x[0]; cells[1] = x[1]; cells[2] = x[2];
-                        for (int t2 = 0; t2 < s.tu; ++t2) {
-                            T acc = T(0);
-                            for (int kk = 0; kk < s.tu; ++kk) acc += tt[kTabHinv + t2 * s.tu + kk] * rT[kk];
-#pragma unroll
-                            for (int kk = 0; kk < BS; ++kk) acc -= tt[kTabHinvE + t2 * BS + kk] * x[kk];
-                            cells[3 + t2] = acc;
-                            o.mfd_cell(q0 + 3 + t2, acc);
-                        }
-                        mfd_nodes_from_window<T>(o, q0 + 1, d.N, cells, q0);
-                    } else {
-                        const T ih = (T)d.inv_h;
-                        const T w0 = (T)mim_w(0), w1 = (T)mim_w(1), w2 = (T)mim_w(2), w3 = (T)mim_w(3);
-                        o.mfd_node(q0 + 1, ih * (w0 * x[0] + w1 * x[1] + w2 * x[2] + w3 * xn[0]));
-                        o.mfd_node(q0 + 2, ih * (w0 * x[1] + w1 * x[2] + w2 * xn[0] + w3 * xn[1]));
-                        o.mfd_node(q0 + 3, ih * (w0 * x[2] + w1 * xn[0] + w2 * xn[1] + w3 * xn[2]));
+                        for (int q = 0; q < BS; ++q) acc -= Gs[k][p][q] * xn[q];
+                        x[p] = acc;
                     }
-                }
+                    const int b = b0 + i;
+                    if constexpr (BS == 2) {
+                        if (k == 0) { pend_node = 3 + b; pend_e = x[0]; pend_g = x[1]; }
+                        else out_cfd(L, 3 + b, x[0], x[1]);
+                        if (last && i == n - 1) cfd_tail_out(L, tt, rT, x[0], x[1]);
+                    } else {
+                        const int q0 = s.hu + 1 + 3 * b;
+                        out_mfd_cell(L, q0, x[0]); out_mfd_cell(L, q0 + 1, x[1]); out_mfd_cell(L, q0 + 2, x[2]);
+                        if (last && i == n - 1) {
+                            mfd_tail_out(L, tt, rT, x, q0);
+                        } else {
+                            const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
+                            out_mfd_node(L, q0 + 1, L.ih * (w0 * x[0] + w1 * x[1] + w2 * x[2] + w3 * xn[0]));
+                            out_mfd_node(L, q0 + 2, L.ih * (w0 * x[1] + w1 * x[2] + w2 * xn[0] + w3 * xn[1]));
+                            out_mfd_node(L, q0 + 3, L.ih * (w0 * x[2] + w1 * xn[0] + w2 * xn[1] + w3 * xn[2]));
+                        }
+                    }
 #pragma unroll
-                for (int p = 0; p < BS; ++p) xn[p] = x[p];
+                    for (int p = 0; p < BS; ++p) xn[p] = x[p];
+                }
             }
         }
+        if constexpr (BS == 2) {
+            if (pend_node >= 0) out_cfd(L, pend_node, pend_e, pend_g);
+            if (first) cfd_head_out(L, th, rH, xn[0], xn[1]);
+        } else {
+            if (first) {
+                mfd_head_out(L, th, rH, xn);
+            } else {  // nodes c_first-2 .. c_first from the left separator and the first block
+                const int q0 = s.hu + 1 + 3 * b0;
+                const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
+                out_mfd_node(L, q0 - 2, L.ih * (w0 * xL[0] + w1 * xL[1] + w2 * xL[2] + w3 * xn[0]));
+                out_mfd_node(L, q0 - 1, L.ih * (w0 * xL[1] + w1 * xL[2] + w2 * xn[0] + w3 * xn[1]));
+                out_mfd_node(L, q0, L.ih * (w0 * xL[2] + w1 * xn[0] + w2 * xn[1] + w3 * xn[2]));
+            }
+        }
+        (void)NSEG;
     }
-    // xn now holds the chunk's first block.  Separator on the right: outputs by this chunk.
-    if (!last) {
+    // the separator on the right of each chunk: outputs after every chunk has read its halo
+    __syncthreads();
+    if (active && !last) {
         const int b = b0 + n;
         if constexpr (BS == 2) {
-            o.cfd_node(3 + b, xR[0], xR[1]);
+            out_cfd(L, 3 + b, xR[0], xR[1]);
         } else {
             const int q0 = s.hu + 1 + 3 * b;
-            o.mfd_cell(q0, xR[0]); o.mfd_cell(q0 + 1, xR[1]); o.mfd_cell(q0 + 2, xR[2]);
+            out_mfd_cell(L, q0, xR[0]); out_mfd_cell(L, q0 + 1, xR[1]); out_mfd_cell(L, q0 + 2, xR[2]);
         }
     }
-    if constexpr (BS == 2) {
-        if (first) {  // head unknowns g0, e1, g1, e2, g2
-            const T *th = d.tab;
-            T xh[5];
-            for (int i = 0; i < 5; ++i) {
-                T acc = T(0);
-                for (int k = 0; k < 5; ++k) acc += th[kTabHinv + i * 5 + k] * rH[k];
-                acc -= th[kTabHinvE + i * 2 + 0] * xn[0] + th[kTabHinvE + i * 2 + 1] * xn[1];
-                xh[i] = acc;
-            }
-            o.cfd_node(0, T(0), xh[0]);
-            o.cfd_node(1, xh[1], xh[2]);
-            o.cfd_node(2, xh[3], xh[4]);
+    if (active && L.src_hit && d.advance_clock) *d.clock = *d.clock + 1;
+    __syncthreads();
+
+    // ---------------- write the staged lines back ----------------
+    {
+        const long long lsp = nl > 1 ? (long long)(descs[desc0 + 1].po - d0.po) : 0;
+        const long long lsv = nl > 1 ? (long long)(descs[desc0 + 1].vo - d0.vo) : 0;
+        const long long spo = d0.spo, svo = d0.svo;
+        T *gp = d0.po, *gv = d0.vo;
+        const int per = blockDim.x / nl;
+        const int lc = tid % nl, kc = tid / nl;
+        if (spo == 1) {
+            for (int ll = 0; ll < nl; ++ll)
+                for (int k = tid; k < np; k += blockDim.x) gp[ll * lsp + k] = sP[ll * Lp + k];
+        } else if (tid < per * nl) {
+            for (int k = kc; k < np; k += per) gp[lc * lsp + k * spo] = sP[lc * Lp + k];
         }
-    } else {
-        if (first) {  // head cells 1..hu, then nodes 0 .. hu+1
-            const T *th = d.tab;
-            T cells[12];
-            cells[0] = d.p[0];
-            for (int i = 0; i < s.hu; ++i) {
-                T acc = T(0);
-                for (int k = 0; k < s.hu; ++k) acc += th[kTabHinv + i * s.hu + k] * rH[k];
-#pragma unroll
-                for (int k = 0; k < BS; ++k) acc -= th[kTabHinvE + i * BS + k] * xn[k];
-                cells[1 + i] = acc;
-                o.mfd_cell(1 + i, acc);
-            }
-            cells[s.hu + 1] = xn[0]; cells[s.hu + 2] = xn[1]; cells[s.hu + 3] = xn[2];
-            mfd_nodes_from_window<T>(o, 0, s.hu + 1, cells, 0);
-        } else {  // nodes c_first-2 .. c_first from the left separator and the first block
-            const int q0 = s.hu + 1 + 3 * b0;
-            T cells[6] = {xL[0], xL[1], xL[2], xn[0], xn[1], xn[2]};
-            const T ih = (T)d.inv_h;
-            const T w0 = (T)mim_w(0), w1 = (T)mim_w(1), w2 = (T)mim_w(2), w3 = (T)mim_w(3);
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj)
-                o.mfd_node(q0 - 2 + jj, ih * (w0 * cells[jj] + w1 * cells[jj + 1] + w2 * cells[jj + 2] + w3 * cells[jj + 3]));
+        if (svo == 1) {
+            for (int ll = 0; ll < nl; ++ll)
+                for (int k = tid; k <= N; k += blockDim.x) gv[ll * lsv + k] = sV[ll * Lp + k];
+        } else if (tid < per * nl) {
+            for (int k = kc; k <= N; k += per) gv[lc * lsv + k * svo] = sV[lc * Lp + k];
         }
     }
 }
@@ -660,6 +924,10 @@ line_solve_chunked_kernel(const LineDesc<T> *__restrict__ descs, const int4 *__r
 
 int chunk_M(int method) { return method == kCFD ? 32 : 16; }
 
+size_t chunked_smem_bytes(int N, int nl, int T, int bs, size_t esz) {
+    return chunked_smem_elems(N, nl, T, bs) * esz;
+}
+
 template <typename T>
 cudaError_t launch_precompute_sep(const LineDesc<T> *d, int nlines, cudaStream_t s) {
     if (nlines <= 0) return cudaSuccess;
@@ -673,7 +941,10 @@ cudaError_t launch_chunked_variant(const LineDesc<T> *d, const int4 *groups, int
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(line_solve_chunked_kernel<T, BS, M, SUB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kChunkSmemMax);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(line_solve_chunked_kernel<T, BS, M, SUB>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }

@@ -19,11 +19,16 @@ struct LineDesc {
     T *po;             // pressure line (output, same indexing as p)
     T *vo;             // velocity line (output, same indexing as v)
     const T *alpha;    // dt/2 * kappa along the pressure line
-    T *u_out;          // natural pressure output (stage-2 lines) or nullptr
+    T *u_out;          // natural pressure output (stage-2 lines) or nullptr; also the
+                       // natural input of the prologue
     T *w_out;          // natural velocity output (stage-2 lines) or nullptr
     const T *tab;      // head/tail elimination tables (kTabLine values)
-    long long sp;      // element stride of p/alpha/u_out along the line
-    long long sv;      // element stride of v/w_out along the line
+    long long sp;      // element stride of p and alpha along the line
+    long long sv;      // element stride of v along the line
+    long long spo;     // element stride of po along the line
+    long long svo;     // element stride of vo along the line
+    long long snp;     // element stride of u_out along the line
+    long long snv;     // element stride of w_out along the line
     int N;             // cells along the line
     int method;        // kCFD / kMFD
     int src_k;         // index along the pressure line of the point source, or -1
@@ -56,9 +61,22 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
 // Scratch words per line of the thread-per-line solver (solution + block factors).
 size_t v1_scratch_words(int method, int N);
 
+// Factored solver (adi_factored.cu).
+bool fac_supported(int method, int N);   // chunk length fits the kernel's registers
+size_t fac_words(int method, int N);     // words of one line's factor record
+int fac_chunks(int method, int N);       // chunks (threads) per line, a power of two
+template <typename T>
+cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, cudaStream_t s);
+template <typename T>
+cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups, int ngroups,
+                                       int method, int threads, int natural, cudaStream_t s);
+
 // Chunked solver (adi_chunked.cu).
 int chunk_M(int method);                 // chunk length in blocks used by the kernel
 int chunk_count(int method, int N, int M);  // chunks per line
+// dynamic shared memory of one CTA of the chunked kernel (nl lines of N cells, T chunks)
+size_t chunked_smem_bytes(int N, int nl, int T, int bs, size_t esz);
+constexpr int kChunkSmemMax = 110 * 1024;  // per CTA, so that two CTAs share an SM
 template <typename T>
 cudaError_t launch_precompute_sep(const LineDesc<T> *d, int nlines, cudaStream_t s);
 template <typename T>

@@ -278,15 +278,15 @@ __device__ void solve_line_v1(const LineDesc<T> &d, T *scr, long long st, int wr
         for (int j = 0; j <= N; ++j) {
             T g = X(cfd_idx_g(N, j));
             T vin = d.v[j * d.sv];
-            d.vo[j * d.sv] = vin - T(2) * beta * g;
-            if (write_natural && d.w_out) d.w_out[j * d.sv] = vin - beta * g;
+            d.vo[j * d.svo] = vin - T(2) * beta * g;
+            if (write_natural && d.w_out) d.w_out[j * d.snv] = vin - beta * g;
         }
         for (int j = 1; j <= N - 1; ++j) {
             T e = X(cfd_idx_e(j));
             T pin = d.p[j * d.sp];
             T ae = L.al(j) * e;
-            d.po[j * d.sp] = pin - T(2) * ae + (j == d.src_k ? src : T(0));
-            if (write_natural && d.u_out) d.u_out[j * d.sp] = pin - ae;
+            d.po[j * d.spo] = pin - T(2) * ae + (j == d.src_k ? src : T(0));
+            if (write_natural && d.u_out) d.u_out[j * d.snp] = pin - ae;
         }
     } else {
         const T ih = (T)d.inv_h;
@@ -303,14 +303,14 @@ __device__ void solve_line_v1(const LineDesc<T> &d, T *scr, long long st, int wr
             }
             T gu = acc * ih;
             T vin = d.v[j * d.sv];
-            d.vo[j * d.sv] = vin - T(2) * beta * gu;
-            if (write_natural && d.w_out) d.w_out[j * d.sv] = vin - beta * gu;
+            d.vo[j * d.svo] = vin - T(2) * beta * gu;
+            if (write_natural && d.w_out) d.w_out[j * d.snv] = vin - beta * gu;
         }
         for (int c = 1; c <= N; ++c) {
             T u = X(c - 1);
             T pin = d.p[c * d.sp];
-            d.po[c * d.sp] = T(2) * u - pin + (c == d.src_k ? src : T(0));
-            if (write_natural && d.u_out) d.u_out[c * d.sp] = u;
+            d.po[c * d.spo] = T(2) * u - pin + (c == d.src_k ? src : T(0));
+            if (write_natural && d.u_out) d.u_out[c * d.snp] = u;
         }
     }
 }
@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(128) line_solve_v1_kernel(const LineDesc<T> *_
 // Prologue: carried state from natural fields, one thread per stage-2 (y) line.
 //   a_k  = u_k - alpha_k (Dv w)_k + dt/2 f(t_m)   (interior pressure points) -> d.po
 //   w*_j = w_j - beta (Du u)_j                      (all velocity points)     -> d.v
-// (d.po of a stage-2 line is the stage-1 input buffer; d.v is the stage-2 input.)
+// (d.po of a stage-2 line is the stage-1 input buffer; d.v is the stage-2 input; the
+// natural u and w are read through d.u_out and d.w_out.)
 // CFD derivatives solve Pbar e = Qbar w and P g = Q u by the Thomas algorithm.
 // ---------------------------------------------------------------------------------------
 template <typename T>
@@ -381,48 +382,49 @@ __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nline
         double t = (double)(*d.clock) * d.dt;
         src = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, t));
     }
+    const long long snp = d.snp, snv = d.snv, spo = d.spo;
     if (d.method == kCFD) {
         // g = P^{-1} Q u  (slots 0..N), then w* = w - beta g
         for (int j = 0; j <= N; ++j) {
             int n = cfd_Q_row(N, j, &c0, w);
             T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * d.sp];
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
             S(j) = acc * ih;
         }
         thomas_apply<T>(N, false, scr, scr + (long long)(N + 1) * st, st);
-        for (int j = 0; j <= N; ++j) d.v[j * d.sv] = wn[j * d.sv] - beta * S(j);
+        for (int j = 0; j <= N; ++j) d.v[j * d.sv] = wn[j * snv] - beta * S(j);
         // e = Pbar^{-1} Qbar w  (slots 0..N-2 for nodes 1..N-1), then a = u - alpha e
         for (int j = 1; j <= N - 1; ++j) {
             int n = cfd_Qbar_row(N, j, &c0, w);
             T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * d.sv];
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
             S(j - 1) = acc * ih;
         }
         thomas_apply<T>(N, true, scr, scr + (long long)(N + 1) * st, st);
         for (int j = 1; j <= N - 1; ++j) {
-            T val = un[j * d.sp] - d.alpha[j * d.sp] * S(j - 1);
+            T val = un[j * snp] - d.alpha[j * d.sp] * S(j - 1);
             if (j == d.src_k) val += src;
-            d.po[j * d.sp] = val;
+            d.po[j * spo] = val;
         }
         d.po[0] = un[0];
-        d.po[(long long)N * d.sp] = un[(long long)N * d.sp];
+        d.po[(long long)N * spo] = un[(long long)N * snp];
     } else {
         for (int j = 0; j <= N; ++j) {
             int n = mfd_G_row(N, j, &c0, w);
             T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * d.sp];
-            d.v[j * d.sv] = wn[j * d.sv] - beta * acc * ih;
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+            d.v[j * d.sv] = wn[j * snv] - beta * acc * ih;
         }
         for (int c = 1; c <= N; ++c) {
             int n = mfd_D_row(N, c - 1, &c0, w);
             T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * d.sv];
-            T val = un[c * d.sp] - d.alpha[c * d.sp] * acc * ih;
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+            T val = un[c * snp] - d.alpha[c * d.sp] * acc * ih;
             if (c == d.src_k) val += src;
-            d.po[c * d.sp] = val;
+            d.po[c * spo] = val;
         }
         d.po[0] = un[0];
-        d.po[(long long)(N + 1) * d.sp] = un[(long long)(N + 1) * d.sp];
+        d.po[(long long)(N + 1) * spo] = un[(long long)(N + 1) * snp];
     }
 }
 

@@ -15,11 +15,16 @@ __device__ __forceinline__ int cfd_idx_e(int j) { return 2 * j - 1; }
 // ---------------------------------------------------------------------------------------
 // Small dense helpers.
 // ---------------------------------------------------------------------------------------
+// Reciprocal: IEEE round-to-nearest in both precisions (the FP32 intrinsic avoids the
+// general division sequence).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 template <typename T, int BS>
 __device__ __forceinline__ void mat_inv(const T (&S)[BS][BS], T (&R)[BS][BS]) {
     if constexpr (BS == 2) {
         T det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
-        T id = T(1) / det;
+        T id = recip(det);
         R[0][0] = S[1][1] * id; R[0][1] = -S[0][1] * id;
         R[1][0] = -S[1][0] * id; R[1][1] = S[0][0] * id;
     } else {
@@ -27,7 +32,7 @@ __device__ __forceinline__ void mat_inv(const T (&S)[BS][BS], T (&R)[BS][BS]) {
         T c01 = S[1][2] * S[2][0] - S[1][0] * S[2][2];
         T c02 = S[1][0] * S[2][1] - S[1][1] * S[2][0];
         T det = S[0][0] * c00 + S[0][1] * c01 + S[0][2] * c02;
-        T id = T(1) / det;
+        T id = recip(det);
         R[0][0] = c00 * id;
         R[0][1] = (S[0][2] * S[2][1] - S[0][1] * S[2][2]) * id;
         R[0][2] = (S[0][1] * S[1][2] - S[0][2] * S[1][1]) * id;
@@ -54,10 +59,16 @@ __device__ __forceinline__ double ricker(double amp, double f0, double tdelay, d
 template <typename T>
 struct Line {
     const LineDesc<T> &d;
-    __device__ Line(const LineDesc<T> &dd) : d(dd) {}
-    __device__ __forceinline__ T p(int k) const { return d.p[k * d.sp]; }
-    __device__ __forceinline__ T v(int k) const { return d.v[k * d.sv]; }
-    __device__ __forceinline__ T al(int k) const { return d.alpha[k * d.sp]; }
+    const T *P, *V, *Al;  // pressure, velocity and alpha lines (global or shared memory)
+    long long sp, sv;
+    __device__ Line(const LineDesc<T> &dd)
+        : d(dd), P(dd.p), V(dd.v), Al(dd.alpha), sp(dd.sp), sv(dd.sv) {}
+    // the same line staged in shared memory (unit strides)
+    __device__ Line(const LineDesc<T> &dd, const T *p, const T *v, const T *al)
+        : d(dd), P(p), V(v), Al(al), sp(1), sv(1) {}
+    __device__ __forceinline__ T p(int k) const { return P[k * sp]; }
+    __device__ __forceinline__ T v(int k) const { return V[k * sv]; }
+    __device__ __forceinline__ T al(int k) const { return Al[k * sp]; }
 };
 
 // Pressure-line length minus one (index of the far Dirichlet value).

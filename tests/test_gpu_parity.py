@@ -106,7 +106,7 @@ def test_standing_wave_fp32(adi, method):
 SIZES = [(16, 16), (17, 23), (18, 16), (40, 29), (61, 64)]
 
 
-@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("solver", [0, 1, 2])
 @pytest.mark.parametrize("method", [CFD, MFD])
 @pytest.mark.parametrize("nx,ny", SIZES)
 def test_random_fields_dirichlet_fp64(adi, method, nx, ny, solver):
@@ -116,7 +116,7 @@ def test_random_fields_dirichlet_fp64(adi, method, nx, ny, solver):
         assert _max_rel(g, o) <= 1e-12
 
 
-@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("solver", [0, 1, 2])
 @pytest.mark.parametrize("method", [CFD, MFD])
 @pytest.mark.parametrize("nx,ny", [(16, 16), (45, 38)])
 def test_random_fields_fp32(adi, method, nx, ny, solver):
@@ -208,25 +208,27 @@ def test_nonfinite_detected(adi):
     s.close()
 
 
-# multi-chunk lines: CFD chunks of <= 32 node blocks, MFD chunks of <= 16 three-cell blocks;
-# these sizes give several chunks per line with ragged last chunks
-MULTI = [(CFD, 230, 171), (MFD, 260, 197), (CFD, 97, 400), (MFD, 53, 311)]
+# multi-chunk lines.  Chunked solver: chunks of <= 32 (CFD) / 16 (MFD) blocks with separators.
+# Factored solver: a power-of-two number of chunks per line of <= 8 (CFD) / 3 (MFD) blocks;
+# these sizes give ragged and empty trailing chunks and lines spanning 1, 2 and more warps.
+MULTI = [(CFD, 230, 171), (MFD, 260, 197), (CFD, 97, 400), (MFD, 53, 311), (CFD, 400, 150),
+         (MFD, 500, 97)]
 
 
+@pytest.mark.parametrize("solver", [1, 2])
 @pytest.mark.parametrize("method,nx,ny", MULTI)
-def test_chunked_multichunk_fp64_vs_oracle(adi, method, nx, ny):
+def test_multichunk_fp64_vs_oracle(adi, method, nx, ny, solver):
     h, dt, c, U, V, W = _random_case(method, nx, ny, seed=nx + ny)
-    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 2, adi.ADI_FP64,
-                     solver=adi.ADI_SOLVER_CHUNKED)
+    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 2, adi.ADI_FP64, solver=solver)
     for g, o in zip(G, O):
         assert _max_rel(g, o) <= 1e-12
 
 
+@pytest.mark.parametrize("solver", [1, 2])
 @pytest.mark.parametrize("method,nx,ny", MULTI)
-def test_chunked_multichunk_fp32_vs_oracle(adi, method, nx, ny):
+def test_multichunk_fp32_vs_oracle(adi, method, nx, ny, solver):
     h, dt, c, U, V, W = _random_case(method, nx, ny, seed=3 * nx + ny)
-    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 4, adi.ADI_FP32,
-                     solver=adi.ADI_SOLVER_CHUNKED)
+    G, O = _run_both(adi, method, nx, ny, h, dt, c, U, V, W, 4, adi.ADI_FP32, solver=solver)
     for g, o in zip(G, O):
         assert _l2_rel(g, o) <= 1e-4
 
@@ -236,7 +238,7 @@ def test_solvers_agree_seismic_with_source(adi, method):
     """Thread-per-line and chunked solvers on a layered medium with a Ricker source."""
     spec = wl.seismic_spec(method, 300, 280, steps=20, h=5.0, seed=9)
     out = []
-    for solver in (adi.ADI_SOLVER_LINE, adi.ADI_SOLVER_CHUNKED):
+    for solver in (adi.ADI_SOLVER_LINE, adi.ADI_SOLVER_CHUNKED, adi.ADI_SOLVER_FACTORED):
         s = adi.Sim(method, spec.nx, spec.ny, spec.h, spec.dt, spec.c, precision=adi.ADI_FP64,
                     solver=solver)
         assert s.solver == solver
@@ -244,8 +246,9 @@ def test_solvers_agree_seismic_with_source(adi, method):
         s.step(20)
         out.append(s.read())
         s.close()
-    for a, b in zip(*out):
-        assert _max_rel(a, b) <= 1e-12
+    for ref in out[1:]:
+        for a, b in zip(out[0], ref):
+            assert _max_rel(a, b) <= 1e-12
 
 
 @pytest.mark.parametrize("method", [CFD, MFD])
