@@ -165,6 +165,36 @@ int adi_batch_sync(adi_batch b);
 int adi_batch_half_step(adi_batch b, int stage, int write_natural);
 int adi_batch_destroy(adi_batch b);
 
+/*
+ * adi_step_static -- one time step (stage 1 then stage 2, no source term) of a small
+ * simulation whose fields the caller keeps in device memory, computed without allocating
+ * anything.  The paper has no counterpart: this is a library service for callers that must
+ * not allocate, e.g. a process whose device memory is wholly pre-reserved by its own pool,
+ * or a latency-bound loop that cannot afford the device-wide synchronisation a cudaFree
+ * implies.  The result equals adi_create + adi_step(1) + adi_read_fields with
+ * ADI_SOLVER_LINE on the same inputs.
+ *   method, nx, ny, h, dt, precision   as for adi_create; nx, ny <= ADI_STATIC_MAX_CELLS.
+ *   c, u, v, w            device arrays of the precision's type (float or double), row-major
+ *                         with the shapes of adi_create (c at U's points, every value > 0,
+ *                         not checked); u's outer rows/columns are the Dirichlet data.
+ *   u_out, v_out, w_out   device arrays with the same shapes, each distinct from every
+ *                         input and from each other; they receive the fields one step later.
+ *   cuda_stream           the work runs on this stream (NULL = legacy default); the call
+ *                         returns after it has finished.
+ * Every temporary (line descriptors, tables, carried state, per-line solver scratch) lives in
+ * one fixed-size array of device memory inside libadi.  The first call on a device looks up
+ * that array's address with the device current; make that first call before any stream
+ * capture begins.  Calls that overlap in time (several host threads, or several streams of
+ * one device) share the array and race: serialise them.
+ * Errors: ADI_EINVAL (bad method/precision, sizes below ADI_MIN_CELLS, h or dt not > 0,
+ * a NULL or aliased pointer); ADI_ENOMEM when nx or ny exceeds ADI_STATIC_MAX_CELLS (the
+ * array's capacity); ADI_ESINGULAR, ADI_ECUDA, ADI_ENOTSUP as elsewhere.
+ */
+#define ADI_STATIC_MAX_CELLS 128
+int adi_step_static(int method, int nx, int ny, double h, double dt, int precision,
+                    const void *c, const void *u, const void *v, const void *w,
+                    void *u_out, void *v_out, void *w_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

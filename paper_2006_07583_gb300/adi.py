@@ -51,6 +51,8 @@ _SIGS = {
     "adi_batch_sync": ([_vp], ctypes.c_int),
     "adi_batch_half_step": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "adi_batch_destroy": ([_vp], ctypes.c_int),
+    "adi_step_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                         ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
 }
 
 
@@ -94,6 +96,12 @@ def _arr(a, shape):
     if a.shape != tuple(shape):
         raise ValueError("expected shape %s, got %s" % (shape, a.shape))
     return a, a.ctypes.data_as(_dp)
+
+
+def step_static(method, nx, ny, h, dt, precision, c, u, v, w, u_out, v_out, w_out, stream=0):
+    """adi_step_static on device pointers (ints): one step into caller-owned device buffers."""
+    _check(lib().adi_step_static(method, nx, ny, h, dt, precision, c, u, v, w, u_out, v_out, w_out,
+                                 stream or None), "adi_step_static")
 
 
 def state_bytes(method, nx, ny, precision=ADI_FP32) -> int:
