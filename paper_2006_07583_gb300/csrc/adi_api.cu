@@ -1,18 +1,23 @@
 // adi_api.cu -- host implementation of the C ABI in include/adi.h.
 //
-// Device state of one simulation (precision T):
-//   A[0]   carried pressure a^m (stage-1 input, stage-2 output), U layout; A[1] holds C
-//          (stage-1 output, stage-2 input).  Outer rows/columns of both hold the Dirichlet data.
-//   V[p]   v^m (natural), V layout; W[p] w* (carried), W layout.  Each half step reads one
-//          copy and writes the other (ping-pong, parity p flips every step), because line
-//          kernels read stencil halos that neighbouring chunks are writing.
-//   alpha  dt/2 * c^2 at U's points.
-//   Uo, Wo natural u, w, written by the last stage-2 launch of every adi_step call.
+// Device state of one simulation (precision T).  Every line kernel reads its lines
+// contiguously: the fields a stage reads are stored with that stage's lines as rows, and
+// the carried pressure changes layout between the stages (each stage writes it transposed).
+//   A[0]   carried pressure a^m (stage-1 input, stage-2 output), row-major U layout.
+//   A[1]   carried C (stage-1 output, stage-2 input), column-major (column j of U is
+//          contiguous, leading dimension rows_u).  Outer rows/columns of both hold the
+//          Dirichlet data.
+//   V[p]   v^m (natural), row-major V layout; W[p] w* (carried), column-major W layout.
+//          Each half step reads one copy and writes the other (ping-pong, parity p flips
+//          every step), because line kernels read stencil halos that neighbouring chunks
+//          are writing.
+//   alpha  dt/2 * c^2 at U's points, row-major; alphaT the same, column-major.
+//   Uo, Wo natural u, w (row-major), written by the last stage-2 launch of every adi_step.
 //   tab    head/tail elimination tables, one kTabLine record per line (rows then columns).
-//   sep    separator-system factors of the chunked solver (per line).
+//   sep    per-line records of the chunked or factored solver.
 // One time step = stage 1 over the x-lines + stage 2 over the y-lines.  Which kernels run is
 // described by an execution plan (Plan): the thread-per-line solver for some members, the
-// chunked solver (one launch per method) for the others.
+// chunked or factored solver (one launch per method) for the others.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,6 +63,7 @@ void dev_free(DevBuf &b) {
 struct Geometry {
     int method, nx, ny;
     int rows_u, ldu, rows_v, ldv, rows_w, ldw;
+    int ldc, ldwc;  // leading dimensions of the column-major copies (rows_u, rows_w)
     int pix, piy;  // interior pressure counts along x and y
     size_t nU() const { return (size_t)rows_u * ldu; }
     size_t nV() const { return (size_t)rows_v * ldv; }
@@ -77,6 +83,8 @@ Geometry make_geometry(int method, int nx, int ny) {
         g.rows_w = ny + 1; g.ldw = nx + 2;
         g.pix = nx; g.piy = ny;
     }
+    g.ldc = g.rows_u;
+    g.ldwc = g.rows_w;
     return g;
 }
 
@@ -179,7 +187,7 @@ struct adi_sim {
     int precision = ADI_FP32;
     double h = 0, dt = 0;
     size_t esz = 4;
-    DevBuf A[2], V[2], W[2], alpha, Uo, Wo, tab, sep, cold_all, clock, status;
+    DevBuf A[2], V[2], W[2], alpha, alphaT, Uo, Wo, tab, sep, cold_all, clock, status;
     int parity = 0;                           // which V/W copy is current
     int plan_base = 0;                        // parity at which the own plan was built
     std::vector<unsigned char> h_desc[2][2];  // host descriptors [parity][0 = x-lines, 1 = y-lines]
@@ -224,6 +232,34 @@ __global__ void convert_to_double(const T *src, double *dst, size_t n) {
     if (i < n) dst[i] = (double)src[i];
 }
 
+// dst[j * ld_dst + i] = src[i * ld_src + j] for a rows x cols array (32 x 32 tiles).
+template <typename T>
+__global__ void transpose_kernel(const T *__restrict__ src, int rows, int cols, int ld_src,
+                                 T *__restrict__ dst, int ld_dst) {
+    __shared__ T tile[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int i = i0 + r, j = j0 + threadIdx.x;
+        if (i < rows && j < cols) tile[r][threadIdx.x] = src[(size_t)i * ld_src + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int j = j0 + r, i = i0 + threadIdx.x;
+        if (i < rows && j < cols) dst[(size_t)j * ld_dst + i] = tile[threadIdx.x][r];
+    }
+}
+
+int transpose(adi_sim *s, const void *src, int rows, int cols, int ld_src, void *dst, int ld_dst) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
+    if (s->precision == ADI_FP64)
+        transpose_kernel<double><<<grid, block, 0, s->stream>>>((const double *)src, rows, cols, ld_src,
+                                                                 (double *)dst, ld_dst);
+    else
+        transpose_kernel<float><<<grid, block, 0, s->stream>>>((const float *)src, rows, cols, ld_src,
+                                                                (float *)dst, ld_dst);
+    return cuda_status(cudaGetLastError());
+}
+
 // Uploads a host double array into a device array of the sim's precision; scale*x or
 // scale*x^2 (used for alpha = dt/2 c^2).  staging must hold n doubles.
 int upload(adi_sim *s, const double *host, void *dst, size_t n, double *staging, double scale,
@@ -250,7 +286,7 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
     T *A0 = (T *)s->A[0].p, *A1 = (T *)s->A[1].p, *Uo = (T *)s->Uo.p, *Wo = (T *)s->Wo.p;
     T *Vi = (T *)s->V[par].p, *Vn = (T *)s->V[1 - par].p;
     T *Wi = (T *)s->W[par].p, *Wn = (T *)s->W[1 - par].p;
-    const T *al = (const T *)s->alpha.p;
+    const T *al = (const T *)s->alpha.p, *alT = (const T *)s->alphaT.p;
     const T *tab = (const T *)s->tab.p;
     T *sep = (T *)s->sep.p;
     const int bs = block_size(g.method);
@@ -277,12 +313,12 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
         int i = r + 1;  // grid row of this x-line
         LineDesc<T> &d = rows[r];
         d.p = A0 + (size_t)i * g.ldu;
-        d.po = A1 + (size_t)i * g.ldu;
+        d.po = A1 + i;  // C is column-major: point j of row i at A1[j * ldc + i]
         d.alpha = al + (size_t)i * g.ldu;
         d.v = Vi + (size_t)i * g.ldv;
         d.vo = Vn + (size_t)i * g.ldv;
         d.u_out = nullptr; d.w_out = nullptr;
-        d.sp = 1; d.sv = 1; d.spo = 1; d.svo = 1; d.snp = 1; d.snv = 1;
+        d.sp = 1; d.sv = 1; d.spo = g.ldc; d.svo = 1; d.snp = 1; d.snv = 1;
         d.N = g.nx;
         d.tab = tab + (size_t)r * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
@@ -293,14 +329,14 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
     for (int c = 0; c < g.pix; ++c) {
         int j = c + 1;  // grid column of this y-line
         LineDesc<T> &d = cols[c];
-        d.p = A1 + j;
-        d.po = A0 + j;
-        d.alpha = al + j;
-        d.v = Wi + j;
-        d.vo = Wn + j;
+        d.p = A1 + (size_t)j * g.ldc;
+        d.po = A0 + j;  // a is row-major
+        d.alpha = alT + (size_t)j * g.ldc;
+        d.v = Wi + (size_t)j * g.ldwc;
+        d.vo = Wn + (size_t)j * g.ldwc;
         d.u_out = Uo + j;
         d.w_out = Wo + j;
-        d.sp = g.ldu; d.sv = g.ldw; d.spo = g.ldu; d.svo = g.ldw; d.snp = g.ldu; d.snv = g.ldw;
+        d.sp = 1; d.sv = 1; d.spo = g.ldu; d.svo = 1; d.snp = g.ldu; d.snv = g.ldw;
         d.N = g.ny;
         d.tab = tab + (size_t)(g.piy + c) * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
@@ -567,10 +603,9 @@ int load_state(adi_sim *s, const double *u, const double *v, const double *w, bo
     if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nV() * esz, cudaMemcpyDeviceToDevice, s->stream));
     if (!rc && (u || !keep_missing)) rc = upload(s, u, s->Uo.p, g.nU(), (double *)staging.p, 1.0, 0);
     if (!rc && (w || !keep_missing)) rc = upload(s, w, s->Wo.p, g.nW(), (double *)staging.p, 1.0, 0);
-    for (int k = 0; k < 2 && !rc; ++k) {
-        rc = cuda_status(cudaMemcpyAsync(s->A[k].p, s->Uo.p, g.nU() * esz, cudaMemcpyDeviceToDevice, s->stream));
-        if (!rc) rc = cuda_status(cudaMemcpyAsync(s->W[k].p, s->Wo.p, g.nW() * esz, cudaMemcpyDeviceToDevice, s->stream));
-    }
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->A[0].p, s->Uo.p, g.nU() * esz, cudaMemcpyDeviceToDevice, s->stream));
+    if (!rc) rc = transpose(s, s->Uo.p, g.rows_u, g.ldu, g.ldu, s->A[1].p, g.ldc);
+    for (int k = 0; k < 2 && !rc; ++k) rc = transpose(s, s->Wo.p, g.rows_w, g.ldw, g.ldw, s->W[k].p, g.ldwc);
     if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
     dev_free(staging);
     if (!rc) rc = upload_sim_descs(s);  // descriptors of the current parity
@@ -621,7 +656,8 @@ size_t adi_state_bytes(int method, int nx, int ny, int precision) {
     Geometry g = make_geometry(method, nx, ny);
     size_t esz = elem_size(precision);
     size_t nl = (size_t)g.pix + g.piy;
-    size_t fields = (3 * g.nU() + g.nV() + 2 * g.nW()) * esz;  // A, alpha, Uo, Vb, Wb, Wo
+    // A, C, alpha, alphaT, Uo; two V copies; two W copies and Wo
+    size_t fields = (5 * g.nU() + 2 * g.nV() + 3 * g.nW()) * esz;
     size_t tab = nl * kTabLine * esz;
     size_t descs = 2 * nl * desc_size(precision);  // sim copy + plan copy
     int sv = default_solver(g, esz);
@@ -661,6 +697,7 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
         if (!rc) rc = dev_alloc(s->W[k], g.nW() * esz);
     }
     if (!rc) rc = dev_alloc(s->alpha, g.nU() * esz);
+    if (!rc) rc = dev_alloc(s->alphaT, g.nU() * esz);
     if (!rc) rc = dev_alloc(s->Uo, g.nU() * esz);
     if (!rc) rc = dev_alloc(s->Wo, g.nW() * esz);
     if (!rc) rc = dev_alloc(s->tab, (size_t)(g.pix + g.piy) * kTabLine * esz);
@@ -671,6 +708,7 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
         DevBuf staging;
         rc = dev_alloc(staging, g.nU() * sizeof(double));
         if (!rc) rc = upload(s, c_field, s->alpha.p, g.nU(), (double *)staging.p, 0.5 * dt, 1);
+        if (!rc) rc = transpose(s, s->alpha.p, g.rows_u, g.ldu, g.ldu, s->alphaT.p, g.ldc);
         if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
         dev_free(staging);
     }
@@ -828,7 +866,7 @@ int adi_destroy(adi_handle s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     plan_free(s->plan);
     DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
-                      &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status};
+                      &s->alphaT, &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status};
     for (DevBuf *b : bufs) dev_free(*b);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     (void)cudaGetLastError();
