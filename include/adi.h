@@ -45,10 +45,11 @@ typedef enum { ADI_FP32 = 0, ADI_FP64 = 1 } adi_precision;
 /* Line solvers:
  *   ADI_SOLVER_LINE      one thread per grid line, factorisation on the fly (the plain path);
  *   ADI_SOLVER_CHUNKED   lines split into chunks joined by a separator system, factorisation
- *                        on the fly (the default where a line fits the kernel's shared
- *                        memory, else FACTORED, else LINE);
- *   ADI_SOLVER_FACTORED  per-line block-LU factors built once in FP64 and kept on the
- *                        device, chunks in registers, chunks joined by scans. */
+ *                        on the fly;
+ *   ADI_SOLVER_FACTORED  per-chunk block-LU records built once in FP64 and kept on the
+ *                        device, line inputs staged by bulk asynchronous copies, chunks in
+ *                        registers joined by scans (the default where the line length allows
+ *                        it, else CHUNKED, else LINE). */
 typedef enum { ADI_SOLVER_LINE = 0, ADI_SOLVER_CHUNKED = 1, ADI_SOLVER_FACTORED = 2 } adi_solver;
 
 typedef enum {

@@ -48,6 +48,17 @@ int cuda_status(cudaError_t e) {
     return ADI_ECUDA;
 }
 
+// Streaming multiprocessors of the current device (persistent grids).
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        (void)cudaGetLastError();
+        return 132;
+    }
+    return n;
+}
+
 int dev_alloc(DevBuf &b, size_t bytes) {
     b.bytes = bytes;
     if (bytes == 0) { b.p = nullptr; return ADI_OK; }
@@ -62,12 +73,19 @@ void dev_free(DevBuf &b) {
 
 struct Geometry {
     int method, nx, ny;
-    int rows_u, ldu, rows_v, ldv, rows_w, ldw;
-    int ldc, ldwc;  // leading dimensions of the column-major copies (rows_u, rows_w)
+    int rows_u, ldu, rows_v, ldv, rows_w, ldw;  // natural (compact, row-major) layouts
+    // carried layouts, leading dimensions padded to 32 elements so that every line starts
+    // on a 128-byte boundary: lda (a and alpha, row-major), ldvp (v, row-major), ldc (C and
+    // alphaT, column-major over U's ldu columns), ldwc (w*, column-major over W's ldw columns)
+    int lda, ldvp, ldc, ldwc;
     int pix, piy;  // interior pressure counts along x and y
     size_t nU() const { return (size_t)rows_u * ldu; }
     size_t nV() const { return (size_t)rows_v * ldv; }
     size_t nW() const { return (size_t)rows_w * ldw; }
+    size_t nA() const { return (size_t)rows_u * lda; }
+    size_t nVp() const { return (size_t)rows_v * ldvp; }
+    size_t nC() const { return (size_t)ldu * ldc; }
+    size_t nWc() const { return (size_t)ldw * ldwc; }
 };
 
 Geometry make_geometry(int method, int nx, int ny) {
@@ -83,8 +101,11 @@ Geometry make_geometry(int method, int nx, int ny) {
         g.rows_w = ny + 1; g.ldw = nx + 2;
         g.pix = nx; g.piy = ny;
     }
-    g.ldc = g.rows_u;
-    g.ldwc = g.rows_w;
+    auto pad = [](int x) { return (x + 31) & ~31; };
+    g.lda = pad(g.ldu);
+    g.ldvp = pad(g.ldv);
+    g.ldc = pad(g.rows_u);
+    g.ldwc = pad(g.rows_w);
     return g;
 }
 
@@ -114,8 +135,8 @@ size_t sep_words(const Geometry &g) {
     return ((size_t)g.piy * (chunks_for(g.method, g.nx) - 1) +
             (size_t)g.pix * (chunks_for(g.method, g.ny) - 1)) * per;
 }
-bool factored_ok(const Geometry &g) {
-    return fac_supported(g.method, g.nx) && fac_supported(g.method, g.ny);
+bool factored_ok(const Geometry &g, size_t esz) {
+    return fac_supported(g.method, g.nx, esz) && fac_supported(g.method, g.ny, esz);
 }
 size_t fac_words_total(const Geometry &g) {
     return (size_t)g.piy * fac_words(g.method, g.nx) + (size_t)g.pix * fac_words(g.method, g.ny);
@@ -132,11 +153,11 @@ size_t v1_words(const Geometry &g) {
     return std::max(v1_scratch_words(g.method, g.nx), v1_scratch_words(g.method, g.ny));
 }
 
-// Measured on GB300 at 4096^2 (FP32, one CFD and one MFD simulation batched): chunked
-// 3.4 ms per step, factored 4.5 ms, thread per line 30 ms.
+// Measured on GB300 at 4096^2 (FP32, one CFD and one MFD simulation batched): factored
+// 1.8 ms per step, chunked 3.2 ms, thread per line 30 ms.
 int default_solver(const Geometry &g, size_t esz) {
+    if (factored_ok(g, esz)) return ADI_SOLVER_FACTORED;
     if (chunked_ok(g, esz)) return ADI_SOLVER_CHUNKED;
-    if (factored_ok(g)) return ADI_SOLVER_FACTORED;
     return ADI_SOLVER_LINE;
 }
 
@@ -157,7 +178,10 @@ struct Plan {
     DevBuf fd[2][2];
     DevBuf fgroups[2][2];
     int nfgroups[2][2] = {{0, 0}, {0, 0}};
-    int fthreads[2][2] = {{0, 0}, {0, 0}};
+    size_t fstage[2][2] = {{0, 0}, {0, 0}};  // shared memory of one pipeline stage
+    int fstages[2][2] = {{0, 0}, {0, 0}};    // pipeline depth (2 = prefetch)
+    int fgrid[2][2] = {{0, 0}, {0, 0}};      // persistent CTAs
+    DevBuf fault;                            // set by a factored launch whose wait ran out
     std::map<int, cudaGraphExec_t> graphs;
 };
 
@@ -172,12 +196,25 @@ void plan_free(Plan &p) {
         for (int q = 0; q < 2; ++q) { dev_free(p.v1d[q][d]); dev_free(p.cd[q][d]); dev_free(p.fd[q][d]); }
         for (int m = 0; m < 2; ++m) { dev_free(p.groups[d][m]); dev_free(p.fgroups[d][m]); }
         p.nfgroups[d][0] = p.nfgroups[d][1] = 0;
-        p.fthreads[d][0] = p.fthreads[d][1] = 0;
+        p.fstage[d][0] = p.fstage[d][1] = 0;
+        p.fstages[d][0] = p.fstages[d][1] = 0;
+        p.fgrid[d][0] = p.fgrid[d][1] = 0;
         p.v1n[d] = 0;
         p.ngroups[d][0] = p.ngroups[d][1] = 0;
         p.smem[d][0] = p.smem[d][1] = 0;
     }
     dev_free(p.scratch);
+    dev_free(p.fault);
+}
+
+// ADI_ETIMEOUT if a launch of the plan gave up waiting for its staged inputs.
+int plan_fault(const Plan &p, cudaStream_t stream) {
+    if (!p.fault.p) return ADI_OK;
+    int f = 0;
+    cudaError_t e = cudaMemcpyAsync(&f, p.fault.p, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return f ? ADI_ETIMEOUT : ADI_OK;
 }
 
 }  // namespace
@@ -218,18 +255,25 @@ struct adi_batch_t {
 
 namespace {
 
+// Compact row-major double (rows x cols) -> rows with leading dimension ld in T.
 template <typename T>
-__global__ void convert_from_double(const double *src, T *dst, size_t n, double scale, int square) {
+__global__ void convert_from_double(const double *src, T *dst, size_t rows, size_t cols, size_t ld,
+                                    double scale, int square) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n) {
+    if (i < rows * cols) {
+        size_t r = i / cols, c = i - r * cols;
         double x = src[i];
-        dst[i] = (T)(square ? scale * x * x : scale * x);
+        dst[r * ld + c] = (T)(square ? scale * x * x : scale * x);
     }
 }
+// Rows with leading dimension ld in T -> compact row-major double.
 template <typename T>
-__global__ void convert_to_double(const T *src, double *dst, size_t n) {
+__global__ void convert_to_double(const T *src, double *dst, size_t rows, size_t cols, size_t ld) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = (double)src[i];
+    if (i < rows * cols) {
+        size_t r = i / cols, c = i - r * cols;
+        dst[i] = (double)src[r * ld + c];
+    }
 }
 
 // dst[j * ld_dst + i] = src[i * ld_src + j] for a rows x cols array (32 x 32 tiles).
@@ -262,8 +306,10 @@ int transpose(adi_sim *s, const void *src, int rows, int cols, int ld_src, void 
 
 // Uploads a host double array into a device array of the sim's precision; scale*x or
 // scale*x^2 (used for alpha = dt/2 c^2).  staging must hold n doubles.
-int upload(adi_sim *s, const double *host, void *dst, size_t n, double *staging, double scale,
-           int square) {
+// (host rows x cols, compact; NULL uploads zeros) -> dst rows with leading dimension ld.
+int upload(adi_sim *s, const double *host, void *dst, size_t rows, size_t cols, size_t ld,
+           double *staging, double scale, int square) {
+    const size_t n = rows * cols;
     if (n == 0) return ADI_OK;
     cudaError_t e;
     if (host)
@@ -273,9 +319,9 @@ int upload(adi_sim *s, const double *host, void *dst, size_t n, double *staging,
     if (e != cudaSuccess) return cuda_status(e);
     unsigned blocks = (unsigned)((n + 255) / 256);
     if (s->precision == ADI_FP64)
-        convert_from_double<double><<<blocks, 256, 0, s->stream>>>(staging, (double *)dst, n, scale, square);
+        convert_from_double<double><<<blocks, 256, 0, s->stream>>>(staging, (double *)dst, rows, cols, ld, scale, square);
     else
-        convert_from_double<float><<<blocks, 256, 0, s->stream>>>(staging, (float *)dst, n, scale, square);
+        convert_from_double<float><<<blocks, 256, 0, s->stream>>>(staging, (float *)dst, rows, cols, ld, scale, square);
     return cuda_status(cudaGetLastError());
 }
 
@@ -312,11 +358,11 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
     for (int r = 0; r < g.piy; ++r) {
         int i = r + 1;  // grid row of this x-line
         LineDesc<T> &d = rows[r];
-        d.p = A0 + (size_t)i * g.ldu;
+        d.p = A0 + (size_t)i * g.lda;
         d.po = A1 + i;  // C is column-major: point j of row i at A1[j * ldc + i]
-        d.alpha = al + (size_t)i * g.ldu;
-        d.v = Vi + (size_t)i * g.ldv;
-        d.vo = Vn + (size_t)i * g.ldv;
+        d.alpha = al + (size_t)i * g.lda;
+        d.v = Vi + (size_t)i * g.ldvp;
+        d.vo = Vn + (size_t)i * g.ldvp;
         d.u_out = nullptr; d.w_out = nullptr;
         d.sp = 1; d.sv = 1; d.spo = g.ldc; d.svo = 1; d.snp = 1; d.snv = 1;
         d.N = g.nx;
@@ -336,7 +382,7 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
         d.vo = Wn + (size_t)j * g.ldwc;
         d.u_out = Uo + j;
         d.w_out = Wo + j;
-        d.sp = 1; d.sv = 1; d.spo = g.ldu; d.svo = 1; d.snp = g.ldu; d.snv = g.ldw;
+        d.sp = 1; d.sv = 1; d.spo = g.lda; d.svo = 1; d.snp = g.ldu; d.snv = g.ldw;
         d.N = g.ny;
         d.tab = tab + (size_t)(g.piy + c) * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
@@ -377,13 +423,12 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                 int first = (int)(fdv[0][dir].size() / dsz);
                 int n = s->nlines[dir];
                 int N = dir == 0 ? s->g.nx : s->g.ny;
-                int Tl = fac_chunks(s->g.method, N);
-                int nl = std::max(1, 512 / Tl);
+                int nl = fac_lines_per_cta(s->g.method, N, esz);
                 for (int st = 0; st < n; st += nl) {
                     int cnt = std::min(nl, n - st);
                     fgr[dir][s->g.method].push_back(make_int4(first + st, cnt, s->g.method, 0));
-                    int th = ((cnt * Tl + 31) / 32) * 32;
-                    p.fthreads[dir][s->g.method] = std::max(p.fthreads[dir][s->g.method], th);
+                    p.fstage[dir][s->g.method] = std::max(p.fstage[dir][s->g.method],
+                                                          fac_stage_bytes(s->g.method, N, cnt, esz));
                 }
                 for (int q = 0; q < 2; ++q) {
                     const std::vector<unsigned char> &h = s->h_desc[s->parity ^ q][dir];
@@ -434,6 +479,9 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
         }
         for (int m = 0; m < 2 && !rc; ++m) {
             p.nfgroups[dir][m] = (int)fgr[dir][m].size();
+            p.fstages[dir][m] = fac_stages_for(p.fstage[dir][m]);
+            p.fgrid[dir][m] = std::min(p.nfgroups[dir][m], sm_count());
+            if (p.nfgroups[dir][m] && !p.fstages[dir][m]) { rc = ADI_ENOTSUP; break; }
             if (!fgr[dir][m].empty()) {
                 rc = dev_alloc(p.fgroups[dir][m], fgr[dir][m].size() * sizeof(int4));
                 if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fgroups[dir][m].p, fgr[dir][m].data(), fgr[dir][m].size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
@@ -447,6 +495,8 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
             }
         }
     }
+    if (!rc) rc = dev_alloc(p.fault, sizeof(int));
+    if (!rc) rc = cuda_status(cudaMemsetAsync(p.fault.p, 0, sizeof(int), stream));
     if (!rc && (p.v1n[0] || p.v1n[1])) {
         p.scratch_stride = std::max(p.v1n[0], p.v1n[1]);
         rc = dev_alloc(p.scratch, words * (size_t)p.scratch_stride * esz);
@@ -469,7 +519,8 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
         if (p.nfgroups[dir][m])
             e = launch_line_solve_factored<T>((const LineDesc<T> *)p.fd[q][dir].p,
                                               (const int4 *)p.fgroups[dir][m].p, p.nfgroups[dir][m], m,
-                                              p.fthreads[dir][m], nat, stream);
+                                              p.fstage[dir][m], p.fstages[dir][m], p.fgrid[dir][m], nat,
+                                              (int *)p.fault.p, stream);
     for (int m = 0; m < 2 && e == cudaSuccess; ++m)
         if (p.ngroups[dir][m])
             e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
@@ -599,11 +650,12 @@ int load_state(adi_sim *s, const double *u, const double *v, const double *w, bo
     int rc = dev_alloc(staging, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
     if (rc) return rc;
     const int cur = s->parity;
-    if (v || !keep_missing) rc = upload(s, v, s->V[cur].p, g.nV(), (double *)staging.p, 1.0, 0);
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nV() * esz, cudaMemcpyDeviceToDevice, s->stream));
-    if (!rc && (u || !keep_missing)) rc = upload(s, u, s->Uo.p, g.nU(), (double *)staging.p, 1.0, 0);
-    if (!rc && (w || !keep_missing)) rc = upload(s, w, s->Wo.p, g.nW(), (double *)staging.p, 1.0, 0);
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->A[0].p, s->Uo.p, g.nU() * esz, cudaMemcpyDeviceToDevice, s->stream));
+    if (v || !keep_missing) rc = upload(s, v, s->V[cur].p, g.rows_v, g.ldv, g.ldvp, (double *)staging.p, 1.0, 0);
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nVp() * esz, cudaMemcpyDeviceToDevice, s->stream));
+    if (!rc && (u || !keep_missing)) rc = upload(s, u, s->Uo.p, g.rows_u, g.ldu, g.ldu, (double *)staging.p, 1.0, 0);
+    if (!rc && (w || !keep_missing)) rc = upload(s, w, s->Wo.p, g.rows_w, g.ldw, g.ldw, (double *)staging.p, 1.0, 0);
+    if (!rc) rc = cuda_status(cudaMemcpy2DAsync(s->A[0].p, g.lda * esz, s->Uo.p, g.ldu * esz, g.ldu * esz,
+                                                g.rows_u, cudaMemcpyDeviceToDevice, s->stream));
     if (!rc) rc = transpose(s, s->Uo.p, g.rows_u, g.ldu, g.ldu, s->A[1].p, g.ldc);
     for (int k = 0; k < 2 && !rc; ++k) rc = transpose(s, s->Wo.p, g.rows_w, g.ldw, g.ldw, s->W[k].p, g.ldwc);
     if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
@@ -656,8 +708,8 @@ size_t adi_state_bytes(int method, int nx, int ny, int precision) {
     Geometry g = make_geometry(method, nx, ny);
     size_t esz = elem_size(precision);
     size_t nl = (size_t)g.pix + g.piy;
-    // A, C, alpha, alphaT, Uo; two V copies; two W copies and Wo
-    size_t fields = (5 * g.nU() + 2 * g.nV() + 3 * g.nW()) * esz;
+    // a, C, alpha, alphaT, Uo; two v copies; two w* copies and Wo
+    size_t fields = (2 * g.nA() + 2 * g.nC() + g.nU() + 2 * g.nVp() + 2 * g.nWc() + g.nW()) * esz;
     size_t tab = nl * kTabLine * esz;
     size_t descs = 2 * nl * desc_size(precision);  // sim copy + plan copy
     int sv = default_solver(g, esz);
@@ -691,15 +743,22 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     s->own_stream = true;
     const size_t esz = s->esz;
     int rc = ADI_OK;
+    rc = dev_alloc(s->A[0], g.nA() * esz);
+    if (!rc) rc = dev_alloc(s->A[1], g.nC() * esz);
     for (int k = 0; k < 2 && !rc; ++k) {
-        rc = dev_alloc(s->A[k], g.nU() * esz);
-        if (!rc) rc = dev_alloc(s->V[k], g.nV() * esz);
-        if (!rc) rc = dev_alloc(s->W[k], g.nW() * esz);
+        rc = dev_alloc(s->V[k], g.nVp() * esz);
+        if (!rc) rc = dev_alloc(s->W[k], g.nWc() * esz);
     }
-    if (!rc) rc = dev_alloc(s->alpha, g.nU() * esz);
-    if (!rc) rc = dev_alloc(s->alphaT, g.nU() * esz);
+    if (!rc) rc = dev_alloc(s->alpha, g.nA() * esz);
+    if (!rc) rc = dev_alloc(s->alphaT, g.nC() * esz);
     if (!rc) rc = dev_alloc(s->Uo, g.nU() * esz);
     if (!rc) rc = dev_alloc(s->Wo, g.nW() * esz);
+    // padding entries are read by bulk copies and the finite check: start them at zero
+    {
+        DevBuf *zb[] = {&s->A[0], &s->A[1], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha, &s->alphaT};
+        for (DevBuf *b : zb)
+            if (!rc) rc = cuda_status(cudaMemsetAsync(b->p, 0, b->bytes, s->stream));
+    }
     if (!rc) rc = dev_alloc(s->tab, (size_t)(g.pix + g.piy) * kTabLine * esz);
     if (!rc) rc = dev_alloc(s->clock, sizeof(long long));
     if (!rc) rc = dev_alloc(s->status, sizeof(int));
@@ -707,8 +766,8 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     if (!rc) {  // alpha = dt/2 c^2
         DevBuf staging;
         rc = dev_alloc(staging, g.nU() * sizeof(double));
-        if (!rc) rc = upload(s, c_field, s->alpha.p, g.nU(), (double *)staging.p, 0.5 * dt, 1);
-        if (!rc) rc = transpose(s, s->alpha.p, g.rows_u, g.ldu, g.ldu, s->alphaT.p, g.ldc);
+        if (!rc) rc = upload(s, c_field, s->alpha.p, g.rows_u, g.ldu, g.lda, (double *)staging.p, 0.5 * dt, 1);
+        if (!rc) rc = transpose(s, s->alpha.p, g.rows_u, g.ldu, g.lda, s->alphaT.p, g.ldc);
         if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
         dev_free(staging);
     }
@@ -725,7 +784,7 @@ int adi_set_solver(adi_handle s, int solver) {
     if (s->sticky) return s->sticky;
     if (s->in_batch) return ADI_EBUSY;
     if (solver == ADI_SOLVER_CHUNKED && !chunked_ok(s->g, s->esz)) return ADI_ENOTSUP;
-    if (solver == ADI_SOLVER_FACTORED && !factored_ok(s->g)) return ADI_ENOTSUP;
+    if (solver == ADI_SOLVER_FACTORED && !factored_ok(s->g, s->esz)) return ADI_ENOTSUP;
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->sticky = cuda_status(e);
     if (solver == s->solver) return ADI_OK;
@@ -784,7 +843,9 @@ int adi_sync(adi_handle s) {
     if (!s) return ADI_EINVAL;
     if (s->sticky) return s->sticky;
     cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) s->sticky = cuda_status(e);
+    if (e != cudaSuccess) return s->sticky = cuda_status(e);
+    int rc = plan_fault(s->plan, s->stream);
+    if (rc) s->sticky = rc;
     return s->sticky;
 }
 
@@ -797,21 +858,24 @@ int adi_read_fields(adi_handle s, double *u, double *v, double *w) {
     int rc = adi_sync(s);
     if (rc) return rc;
     const Geometry &g = s->g;
-    struct { const void *src; double *dst; size_t n; } parts[3] = {
-        {s->Uo.p, u, g.nU()}, {s->V[s->parity].p, v, g.nV()}, {s->Wo.p, w, g.nW()}};
+    struct { const void *src; double *dst; size_t rows, cols, ld; } parts[3] = {
+        {s->Uo.p, u, (size_t)g.rows_u, (size_t)g.ldu, (size_t)g.ldu},
+        {s->V[s->parity].p, v, (size_t)g.rows_v, (size_t)g.ldv, (size_t)g.ldvp},
+        {s->Wo.p, w, (size_t)g.rows_w, (size_t)g.ldw, (size_t)g.ldw}};
     DevBuf tmp;
     rc = dev_alloc(tmp, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
     if (rc) return rc;
     for (auto &pt : parts) {
         if (!pt.dst) continue;
-        unsigned blocks = (unsigned)((pt.n + 255) / 256);
+        const size_t n = pt.rows * pt.cols;
+        unsigned blocks = (unsigned)((n + 255) / 256);
         if (s->precision == ADI_FP64)
-            convert_to_double<double><<<blocks, 256, 0, s->stream>>>((const double *)pt.src, (double *)tmp.p, pt.n);
+            convert_to_double<double><<<blocks, 256, 0, s->stream>>>((const double *)pt.src, (double *)tmp.p, pt.rows, pt.cols, pt.ld);
         else
-            convert_to_double<float><<<blocks, 256, 0, s->stream>>>((const float *)pt.src, (double *)tmp.p, pt.n);
+            convert_to_double<float><<<blocks, 256, 0, s->stream>>>((const float *)pt.src, (double *)tmp.p, pt.rows, pt.cols, pt.ld);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(pt.dst, tmp.p, pt.n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            e = cudaMemcpyAsync(pt.dst, tmp.p, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) { dev_free(tmp); return s->sticky = cuda_status(e); }
     }
@@ -841,7 +905,7 @@ int adi_check_finite(adi_handle s) {
     cudaError_t e = cudaMemsetAsync(s->status.p, 0, sizeof(int), s->stream);
     const Geometry &g = s->g;
     const void *fields[4] = {s->A[0].p, s->V[s->parity].p, s->W[s->parity].p, s->Uo.p};
-    size_t ns[4] = {g.nU(), g.nV(), g.nW(), g.nU()};
+    size_t ns[4] = {g.nA(), g.nVp(), g.nWc(), g.nU()};
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         e = s->precision == ADI_FP64
                 ? launch_finite_check<double>((const double *)fields[k], ns[k], (int *)s->status.p, s->stream)
@@ -948,7 +1012,9 @@ int adi_batch_sync(adi_batch b) {
     if (b->sticky) return b->sticky;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return batch_fail(b, e);
-    return ADI_OK;
+    int rc = plan_fault(b->plan, b->stream);
+    if (rc) b->sticky = rc;
+    return rc;
 }
 
 int adi_batch_destroy(adi_batch b) {

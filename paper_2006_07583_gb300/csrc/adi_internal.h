@@ -39,7 +39,7 @@ struct LineDesc {
     double dt;
     double src_amp, src_f0, src_tdelay; // Ricker source (amp, f0, delay)
     double src_scale;  // dt / (2 h^2)
-    T *sep;            // separator-system factors of the chunked solver (this line)
+    T *sep;            // per-line record of the chunked or factored solver
     int chunkM;        // chunk length (blocks) the separator factors were built for
     int pad2;
 };
@@ -62,14 +62,18 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
 size_t v1_scratch_words(int method, int N);
 
 // Factored solver (adi_factored.cu).
-bool fac_supported(int method, int N);   // chunk length fits the kernel's registers
-size_t fac_words(int method, int N);     // words of one line's factor record
+bool fac_supported(int method, int N, size_t esz);  // chunk fits registers, stage fits smem
+size_t fac_words(int method, int N);     // elements of one line's chunk record
 int fac_chunks(int method, int N);       // chunks (threads) per line, a power of two
+int fac_lines_per_cta(int method, int N, size_t esz);
+size_t fac_stage_bytes(int method, int N, int nl, size_t esz);  // shared memory of one stage
+int fac_stages_for(size_t stage_bytes);  // 2 (prefetch), 1, or 0 (does not fit)
 template <typename T>
 cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, cudaStream_t s);
 template <typename T>
 cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups, int ngroups,
-                                       int method, int threads, int natural, cudaStream_t s);
+                                       int method, size_t stage_bytes, int stages, int grid,
+                                       int natural, int *fault, cudaStream_t s);
 
 // Chunked solver (adi_chunked.cu).
 int chunk_M(int method);                 // chunk length in blocks used by the kernel
