@@ -70,8 +70,13 @@ __host__ __device__ inline int fac_line_elems(int method, int N) {
     return 3 * fac_lp(N) + fac_rec(s.bs, fac_geom(method, N).T);
 }
 
+// One stage: the group's descriptors, then per line [p | v | alpha | record].
+constexpr size_t kDescBytes = sizeof(LineDesc<float>);
+static_assert(sizeof(LineDesc<float>) == sizeof(LineDesc<double>), "descriptor sizes differ");
+static_assert(kDescBytes % 16 == 0, "descriptor size");
+__host__ __device__ inline size_t fac_desc_area(int nl) { return ((size_t)nl * kDescBytes + 127) & ~(size_t)127; }
 size_t fac_stage_bytes(int method, int N, int nl, size_t esz) {
-    size_t b = (size_t)nl * fac_line_elems(method, N) * esz;
+    size_t b = fac_desc_area(nl) + (size_t)nl * fac_line_elems(method, N) * esz;
     return (b + 127) & ~(size_t)127;
 }
 int fac_stages_for(size_t stage_bytes) {
@@ -488,8 +493,10 @@ __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, int4 gr, unsign
     const unsigned bp = round16((unsigned)(p_last(method, N) + 1) * (unsigned)sizeof(T));
     const unsigned bv = round16((unsigned)(N + 1) * (unsigned)sizeof(T));
     const unsigned br = (unsigned)R * (unsigned)sizeof(T);
-    mbar_expect_tx(bar, (unsigned)gr.y * (2 * bp + bv + br));
-    T *base = (T *)stage;
+    const unsigned bd = (unsigned)(gr.y * kDescBytes);
+    mbar_expect_tx(bar, bd + (unsigned)gr.y * (2 * bp + bv + br));
+    bulk_to_smem(stage, descs + gr.x, bd, bar);
+    T *base = (T *)(stage + fac_desc_area(gr.y));
     for (int l = 0; l < gr.y; ++l) {
         const LineDesc<T> &d = descs[gr.x + l];
         T *ln = base + (size_t)l * (3 * Lp + R);
@@ -500,16 +507,38 @@ __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, int4 gr, unsign
     }
 }
 
+// W consecutive elements of shared memory into registers: 16-byte loads where src is
+// 16-byte aligned, element loads otherwise.
+template <typename T, int W>
+__device__ __forceinline__ void load_window(const T *src, T (&w)[W]) {
+    constexpr int per = 16 / (int)sizeof(T);
+    static_assert(W % per == 0, "window");
+    if ((smem_addr(src) & 15u) == 0) {
+#pragma unroll
+        for (int k = 0; k < W; k += per) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(src + k);
+            const T *e = reinterpret_cast<const T *>(&q);
+#pragma unroll
+            for (int j = 0; j < per; ++j) w[k + j] = e[j];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) w[k] = src[k];
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // One line group from its staged inputs.  nl lines of one simulation and direction, T
 // threads per line; thread (l, c) = (tid / T, tid % T) owns blocks [c M, c M + M) of line l.
 // ---------------------------------------------------------------------------------------
 template <typename T, int BS, int MM>
-__device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs, int4 gr,
-                                          const T *stage, int natural, Map<T, BS> *smmaps) {
+__device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_raw, int natural,
+                                          Map<T, BS> *smmaps) {
     constexpr int B2 = BS * BS;
     const int tid = threadIdx.x;
-    const LineDesc<T> &d0 = descs[gr.x];
+    const LineDesc<T> *descs = (const LineDesc<T> *)stage_raw;  // staged descriptors
+    const T *stage = (const T *)(stage_raw + fac_desc_area(gr.y));
+    const LineDesc<T> &d0 = descs[0];
     const int N = d0.N;
     const LineShape s = line_shape(d0.method, N);
     const FGeom g = fgeom(s.nb, fac_mmax(d0.method));
@@ -517,7 +546,7 @@ __device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs,
     const int Lp = fac_lp(N), R = fac_rec(BS, Tl);
     const int l = tid / Tl, c = tid % Tl;
     const bool active = l < gr.y;
-    const LineDesc<T> &d = descs[gr.x + (active ? l : 0)];
+    const LineDesc<T> &d = descs[active ? l : 0];
     const T *sP = stage + (size_t)(active ? l : 0) * (3 * Lp + R);
     const T *sV = sP + Lp, *sA = sP + 2 * Lp, *sR = sP + 3 * Lp;
     const T *eH = sR + fac_chunk_elems(BS, Tl), *eT = eH + kEndStride;  // end tables
@@ -535,22 +564,43 @@ __device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs,
     T aw[NA];     // CFD: 3 alpha / h at nodes b0+2 ..;  MFD: alpha at the chunk's cells
     T Y[MM][BS];  // r, then y, then x
     const int cb = s.hu + 1 + 3 * b0;  // MFD: first cell of the chunk
-    {
-        const int na = (BS == 2) ? n + 2 : 3 * n;
+    if constexpr (BS == 2) {
+        // windows s[b0 .. b0+MM+3] (the reads stay inside the stage buffer)
+        static_assert(MM % 4 == 0, "CFD window length");
         const T c3 = T(3) * ih;
+        // node j = b0 + i + 3 is window index i + 3
+        {
+            T w[MM + 4];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            const T a = (k < na) ? sA[(BS == 2 ? b0 + 2 : cb) + k] : T(0);
-            aw[k] = (BS == 2) ? c3 * a : a;
+            for (int k = 0; k < MM + 4; ++k) w[k] = T(0);
+            if (n > 0) load_window<T, MM + 4>(sA + b0, w);
+#pragma unroll
+            for (int k = 0; k < NA; ++k) aw[k] = (k < n + 2) ? c3 * w[k + 2] : T(0);
         }
+        {
+            T w[MM + 4];
+#pragma unroll
+            for (int k = 0; k < MM + 4; ++k) w[k] = T(0);
+            if (n > 0) load_window<T, MM + 4>(sV + b0, w);
+#pragma unroll
+            for (int i = 0; i < MM; ++i) Y[i][0] = (i < n) ? c3 * (w[i + 4] - w[i + 2]) : T(0);
+        }
+        {
+            T w[MM + 4];
+#pragma unroll
+            for (int k = 0; k < MM + 4; ++k) w[k] = T(0);
+            if (n > 0) load_window<T, MM + 4>(sP + b0, w);
+#pragma unroll
+            for (int i = 0; i < MM; ++i) Y[i][1] = (i < n) ? c3 * (w[i + 4] - w[i + 2]) : T(0);
+        }
+    } else {
+        const int na = 3 * n;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) aw[k] = (k < na) ? sA[cb + k] : T(0);
 #pragma unroll
         for (int i = 0; i < MM; ++i) {
             if (i < n) {
-                if constexpr (BS == 2) {
-                    const int j = b0 + i + 3;
-                    Y[i][0] = c3 * (sV[j + 1] - sV[j - 1]);
-                    Y[i][1] = c3 * (sP[j + 1] - sP[j - 1]);
-                } else {
+                {
                     const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
 #pragma unroll
                     for (int m = 0; m < 3; ++m) {
@@ -566,7 +616,7 @@ __device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs,
         }
     }
     // end windows z = [p window, v window, x of the adjacent block] (x filled later)
-    auto load_window = [&](bool tail, T (&z)[19]) {
+    auto end_window = [&](bool tail, T (&z)[19]) {
         const int op = tail ? pl - 7 : 0, ov = tail ? N - 7 : 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) { z[k] = sP[op + k]; z[8 + k] = sV[ov + k]; }
@@ -575,7 +625,7 @@ __device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs,
     };
     if (has_first) {  // head elimination: r_0 += KZ_head z
         T z[19];
-        load_window(false, z);
+        end_window(false, z);
 #pragma unroll
         for (int p = 0; p < BS; ++p) {
             T acc = T(0);
@@ -586,7 +636,7 @@ __device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs,
     }
     if (has_last) {  // tail elimination: r_{nb-1} += KZ_tail z
         T z[19];
-        load_window(true, z);
+        end_window(true, z);
         const int il = n - 1;
 #pragma unroll
         for (int p = 0; p < BS; ++p) {
@@ -842,37 +892,58 @@ __device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs,
 
     // ---- outputs: C = 2 u* - a (+ source), v' = 2 v* - v, optionally natural u, w ----
     bool hit = false;
+    const int src_k = d.src_k;
     auto srcval = [&](int k) -> T {
-        if (k != d.src_k) return T(0);
+        if (k != src_k) return T(0);
         hit = true;
         const long long m = *d.clock;
         return (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(m + 1) * d.dt));
     };
-    const bool nat = natural && d.u_out != nullptr;
-    T *gpo = d.po, *gvo = d.vo;
-    const int spo = (int)d.spo, svo = (int)d.svo;
+    T *__restrict__ uo = natural ? d.u_out : nullptr;
+    T *__restrict__ wo = natural ? d.w_out : nullptr;
+    const bool nat = uo != nullptr;
+    T *__restrict__ gpo = d.po;
+    T *__restrict__ gvo = d.vo;
+    const int spo = (int)d.spo, svo = (int)d.svo, snp = (int)d.snp, snv = (int)d.snv;
     auto out_p = [&](int k, T val_out, T val_nat) {
         gpo[k * spo] = val_out + srcval(k);
-        if (nat) d.u_out[k * (int)d.snp] = val_nat;
+        if (nat) uo[k * snp] = val_nat;
     };
     auto out_v = [&](int j, T vin, T dv) {  // dv = beta * (D_u u*)_j
         gvo[j * svo] = vin - T(2) * dv;
-        if (nat) d.w_out[j * (int)d.snv] = vin - dv;
+        if (nat) wo[j * snv] = vin - dv;
     };
-    T xn[BS];  // x of the block after the current one
+    if constexpr (BS == 2) {
+        // node j = b0 + i + 3 is window index i + 3 (16-byte loads of the chunk's windows)
+        {
+            T wp[MM + 4], wa[MM + 4];
+            if (n > 0) {
+                load_window<T, MM + 4>(sP + b0, wp);
+                load_window<T, MM + 4>(sA + b0, wa);
+            }
 #pragma unroll
-    for (int p = 0; p < BS; ++p) xn[p] = xin[p];
+            for (int i = 0; i < MM; ++i)
+                if (i < n) {
+                    const T pin = wp[i + 3];
+                    const T ae = wa[i + 3] * Y[i][0];
+                    out_p(b0 + i + 3, pin - T(2) * ae, pin - ae);
+                }
+        }
+        {
+            T wv[MM + 4];
+            if (n > 0) load_window<T, MM + 4>(sV + b0, wv);
 #pragma unroll
-    for (int i = MM - 1; i >= 0; --i) {
-        if (i < n) {
-            const int b = b0 + i;
-            if constexpr (BS == 2) {
-                const int j = b + 3;
-                const T pin = sP[j];
-                const T ae = sA[j] * Y[i][0];
-                out_p(j, pin - T(2) * ae, pin - ae);
-                out_v(j, sV[j], beta * Y[i][1]);
-            } else {
+            for (int i = 0; i < MM; ++i)
+                if (i < n) out_v(b0 + i + 3, wv[i + 3], beta * Y[i][1]);
+        }
+    } else {
+        T xn[BS];  // x of the block after the current one
+#pragma unroll
+        for (int p = 0; p < BS; ++p) xn[p] = xin[p];
+#pragma unroll
+        for (int i = MM - 1; i >= 0; --i) {
+            if (i < n) {
+                const int b = b0 + i;
                 const int q0 = cb + 3 * i;
 #pragma unroll
                 for (int m = 0; m < 3; ++m) out_p(q0 + m, T(2) * Y[i][m] - sP[q0 + m], Y[i][m]);
@@ -884,57 +955,65 @@ __device__ __forceinline__ void fac_group(const LineDesc<T> *__restrict__ descs,
                     out_v(q0 + 2, sV[q0 + 2], bi * (w0 * Y[i][1] + w1 * Y[i][2] + w2 * xn[0] + w3 * xn[1]));
                     out_v(q0 + 3, sV[q0 + 3], bi * (w0 * Y[i][2] + w1 * xn[0] + w2 * xn[1] + w3 * xn[2]));
                 }
+#pragma unroll
+                for (int p = 0; p < BS; ++p) xn[p] = Y[i][p];
             }
-            if (b == s.nb - 1) {  // tail unknowns: xe = HZ z, z with this block's x
-                T z[19], xe[6];
-                load_window(true, z);
+        }
+    }
+    T xl[BS];  // x of the chunk's last block
 #pragma unroll
-                for (int p = 0; p < BS; ++p) z[16 + p] = Y[i][p];
+    for (int p = 0; p < BS; ++p) xl[p] = Y[0][p];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    T acc = T(0);
+    for (int i = 1; i < MM; ++i)
+        if (i == n - 1)
 #pragma unroll
-                    for (int k = 0; k < 19; ++k) acc += eT[kEndHZ + q * 19 + k] * z[k];
-                    xe[q] = acc;
-                }
-                if constexpr (BS == 2) {
-                    // e_{N-2}, g_{N-2}, e_{N-1}, g_{N-1}, g_N
+            for (int p = 0; p < BS; ++p) xl[p] = Y[i][p];
+    if (has_last) {  // tail unknowns: xe = HZ z, z with the last block's x
+        T z[19], xe[6];
+        end_window(true, z);
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int j = N - 2 + q;
-                        const T pin = sP[j];
-                        const T ae = sA[j] * xe[2 * q];
-                        out_p(j, pin - T(2) * ae, pin - ae);
-                        out_v(j, sV[j], beta * xe[2 * q + 1]);
-                    }
-                    out_v(N, sV[N], beta * xe[4]);
-                } else {
-                    // tail cells after this block, then nodes qb+1 .. N
-                    const int qb = cb + 3 * i;
-                    for (int t2 = 0; t2 < s.tu; ++t2) {
-                        const int cc = qb + 3 + t2;
-                        T xv = xe[0];
+        for (int p = 0; p < BS; ++p) z[16 + p] = xl[p];
 #pragma unroll
-                        for (int q = 1; q < 6; ++q)
-                            if (q == t2) xv = xe[q];
-                        out_p(cc, T(2) * xv - sP[cc], xv);
-                    }
-                    for (int j = qb + 1; j <= N; ++j) {
-                        const T *row = eT + kEndDZ + (j - qb - 1) * 19;
-                        T acc = T(0);
+        for (int q = 0; q < 6; ++q) {
+            T acc = T(0);
 #pragma unroll
-                        for (int k = 0; k < 19; ++k) acc += row[k] * z[k];
-                        out_v(j, sV[j], beta * ih * acc);
-                    }
-                }
+            for (int k = 0; k < 19; ++k) acc += eT[kEndHZ + q * 19 + k] * z[k];
+            xe[q] = acc;
+        }
+        if constexpr (BS == 2) {
+            // e_{N-2}, g_{N-2}, e_{N-1}, g_{N-1}, g_N
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int j = N - 2 + q;
+                const T pin = sP[j];
+                const T ae = sA[j] * xe[2 * q];
+                out_p(j, pin - T(2) * ae, pin - ae);
+                out_v(j, sV[j], beta * xe[2 * q + 1]);
             }
+            out_v(N, sV[N], beta * xe[4]);
+        } else {
+            // tail cells after this block, then nodes qb+1 .. N
+            const int qb = cb + 3 * (n - 1);
+            for (int t2 = 0; t2 < s.tu; ++t2) {
+                const int cc = qb + 3 + t2;
+                T xv = xe[0];
 #pragma unroll
-            for (int p = 0; p < BS; ++p) xn[p] = Y[i][p];
+                for (int q = 1; q < 6; ++q)
+                    if (q == t2) xv = xe[q];
+                out_p(cc, T(2) * xv - sP[cc], xv);
+            }
+            for (int j = qb + 1; j <= N; ++j) {
+                const T *row = eT + kEndDZ + (j - qb - 1) * 19;
+                T acc = T(0);
+#pragma unroll
+                for (int k = 0; k < 19; ++k) acc += row[k] * z[k];
+                out_v(j, sV[j], beta * ih * acc);
+            }
         }
     }
     if (has_first) {  // head unknowns from block 0: xe = HZ z, z with block 0's x
         T z[19], xe[6];
-        load_window(false, z);
+        end_window(false, z);
 #pragma unroll
         for (int p = 0; p < BS; ++p) z[16 + p] = Y[0][p];
 #pragma unroll
@@ -1010,8 +1089,7 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const int4 *__
         }
         const bool got = mbar_wait(&bars[st], par);
         if (!__syncthreads_and(got)) { ok = false; break; }
-        fac_group<T, BS, MM>(descs, groups[g], (const T *)(fac_smem + (size_t)st * stage_bytes), natural,
-                             smmaps);
+        fac_group<T, BS, MM>(groups[g], fac_smem + (size_t)st * stage_bytes, natural, smmaps);
         __syncthreads();
     }
     if (!ok && tid == 0) {

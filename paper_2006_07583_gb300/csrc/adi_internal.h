@@ -13,7 +13,7 @@ namespace adi {
 // Inputs (p, v) and outputs (po, vo) are distinct buffers: line kernels read stencil halos
 // of neighbouring chunks while other chunks write, so a half step never updates in place.
 template <typename T>
-struct LineDesc {
+struct alignas(16) LineDesc {  // 16-byte multiple: descriptor arrays are bulk-copied
     T *p;              // pressure line (input), element 0 and element L are the Dirichlet values
     T *v;              // velocity line v_0..v_N (input)
     T *po;             // pressure line (output, same indexing as p)
