@@ -174,13 +174,14 @@ struct Plan {
     DevBuf groups[2][2];
     int ngroups[2][2] = {{0, 0}, {0, 0}};
     size_t smem[2][2] = {{0, 0}, {0, 0}};
-    // factored members: descriptors per [parity][direction], groups per [dir][method]
+    // factored members: descriptors per [parity][direction], groups per [dir][kernel variant]
     DevBuf fd[2][2];
-    DevBuf fgroups[2][2];
-    int nfgroups[2][2] = {{0, 0}, {0, 0}};
-    size_t fstage[2][2] = {{0, 0}, {0, 0}};  // shared memory of one pipeline stage
-    int fstages[2][2] = {{0, 0}, {0, 0}};    // pipeline depth (2 = prefetch)
-    int fgrid[2][2] = {{0, 0}, {0, 0}};      // persistent CTAs
+    DevBuf fgroups[2][kFacVariants];
+    int nfgroups[2][kFacVariants] = {};
+    size_t fstage[2][kFacVariants] = {};  // shared memory of one pipeline stage
+    int fstages[2][kFacVariants] = {};    // pipeline depth (2 = prefetch)
+    int fgrid[2][kFacVariants] = {};      // persistent CTAs
+    int freach[2][kFacVariants] = {};     // largest scan reach of the launch's lines
     DevBuf fault;                            // set by a factored launch whose wait ran out
     std::map<int, cudaGraphExec_t> graphs;
 };
@@ -194,11 +195,15 @@ void plan_free(Plan &p) {
     drop_graphs(p.graphs);
     for (int d = 0; d < 2; ++d) {
         for (int q = 0; q < 2; ++q) { dev_free(p.v1d[q][d]); dev_free(p.cd[q][d]); dev_free(p.fd[q][d]); }
-        for (int m = 0; m < 2; ++m) { dev_free(p.groups[d][m]); dev_free(p.fgroups[d][m]); }
-        p.nfgroups[d][0] = p.nfgroups[d][1] = 0;
-        p.fstage[d][0] = p.fstage[d][1] = 0;
-        p.fstages[d][0] = p.fstages[d][1] = 0;
-        p.fgrid[d][0] = p.fgrid[d][1] = 0;
+        for (int m = 0; m < 2; ++m) dev_free(p.groups[d][m]);
+        for (int v = 0; v < kFacVariants; ++v) {
+            dev_free(p.fgroups[d][v]);
+            p.nfgroups[d][v] = 0;
+            p.fstage[d][v] = 0;
+            p.fstages[d][v] = 0;
+            p.fgrid[d][v] = 0;
+            p.freach[d][v] = 0;
+        }
         p.v1n[d] = 0;
         p.ngroups[d][0] = p.ngroups[d][1] = 0;
         p.smem[d][0] = p.smem[d][1] = 0;
@@ -230,6 +235,7 @@ struct adi_sim {
     std::vector<unsigned char> h_desc[2][2];  // host descriptors [parity][0 = x-lines, 1 = y-lines]
     int nlines[2] = {0, 0};
     int solver = ADI_SOLVER_CHUNKED;
+    int fac_reach = 0;                        // largest scan reach of the factored records
     Plan plan;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -410,7 +416,7 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
     p.precision = prec;
     const size_t dsz = desc_size(prec), esz = elem_size(prec);
     std::vector<unsigned char> v1[2][2], cd[2][2], fdv[2][2];
-    std::vector<int4> gr[2][2], fgr[2][2];
+    std::vector<int4> gr[2][2], fgr[2][kFacVariants];
     size_t words = 0;
     for (adi_sim *s : members) {
         for (int dir = 0; dir < 2; ++dir) {
@@ -424,12 +430,13 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                 int n = s->nlines[dir];
                 int N = dir == 0 ? s->g.nx : s->g.ny;
                 int nl = fac_lines_per_cta(s->g.method, N, esz);
+                int v = fac_variant(s->g.method, N);
                 for (int st = 0; st < n; st += nl) {
                     int cnt = std::min(nl, n - st);
-                    fgr[dir][s->g.method].push_back(make_int4(first + st, cnt, s->g.method, 0));
-                    p.fstage[dir][s->g.method] = std::max(p.fstage[dir][s->g.method],
-                                                          fac_stage_bytes(s->g.method, N, cnt, esz));
+                    fgr[dir][v].push_back(make_int4(first + st, cnt, s->g.method, 0));
+                    p.fstage[dir][v] = std::max(p.fstage[dir][v], fac_stage_bytes(s->g.method, N, cnt, esz));
                 }
+                p.freach[dir][v] = std::max(p.freach[dir][v], s->fac_reach);
                 for (int q = 0; q < 2; ++q) {
                     const std::vector<unsigned char> &h = s->h_desc[s->parity ^ q][dir];
                     fdv[q][dir].insert(fdv[q][dir].end(), h.begin(), h.end());
@@ -477,14 +484,14 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                 if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fd[q][dir].p, fdv[q][dir].data(), fdv[q][dir].size(), cudaMemcpyHostToDevice, stream));
             }
         }
-        for (int m = 0; m < 2 && !rc; ++m) {
-            p.nfgroups[dir][m] = (int)fgr[dir][m].size();
-            p.fstages[dir][m] = fac_stages_for(p.fstage[dir][m]);
-            p.fgrid[dir][m] = std::min(p.nfgroups[dir][m], sm_count());
-            if (p.nfgroups[dir][m] && !p.fstages[dir][m]) { rc = ADI_ENOTSUP; break; }
-            if (!fgr[dir][m].empty()) {
-                rc = dev_alloc(p.fgroups[dir][m], fgr[dir][m].size() * sizeof(int4));
-                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fgroups[dir][m].p, fgr[dir][m].data(), fgr[dir][m].size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+        for (int v = 0; v < kFacVariants && !rc; ++v) {
+            p.nfgroups[dir][v] = (int)fgr[dir][v].size();
+            p.fstages[dir][v] = fac_stages_for(p.fstage[dir][v], esz);
+            p.fgrid[dir][v] = std::min(p.nfgroups[dir][v], sm_count());
+            if (p.nfgroups[dir][v] && !p.fstages[dir][v]) { rc = ADI_ENOTSUP; break; }
+            if (!fgr[dir][v].empty()) {
+                rc = dev_alloc(p.fgroups[dir][v], fgr[dir][v].size() * sizeof(int4));
+                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fgroups[dir][v].p, fgr[dir][v].data(), fgr[dir][v].size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
             }
         }
         for (int m = 0; m < 2 && !rc; ++m) {
@@ -515,12 +522,12 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
     if (p.v1n[dir])
         e = launch_line_solve_v1<T>((const LineDesc<T> *)p.v1d[q][dir].p, p.v1n[dir], (T *)p.scratch.p,
                                     p.scratch_stride, nat, stream);
-    for (int m = 0; m < 2 && e == cudaSuccess; ++m)
-        if (p.nfgroups[dir][m])
+    for (int v = 0; v < kFacVariants && e == cudaSuccess; ++v)
+        if (p.nfgroups[dir][v])
             e = launch_line_solve_factored<T>((const LineDesc<T> *)p.fd[q][dir].p,
-                                              (const int4 *)p.fgroups[dir][m].p, p.nfgroups[dir][m], m,
-                                              p.fstage[dir][m], p.fstages[dir][m], p.fgrid[dir][m], nat,
-                                              (int *)p.fault.p, stream);
+                                              (const int4 *)p.fgroups[dir][v].p, p.nfgroups[dir][v], v,
+                                              p.fstage[dir][v], p.fstages[dir][v], p.fgrid[dir][v], nat,
+                                              p.freach[dir][v], (int *)p.fault.p, stream);
     for (int m = 0; m < 2 && e == cudaSuccess; ++m)
         if (p.ngroups[dir][m])
             e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
@@ -620,8 +627,18 @@ int run_precompute(adi_sim *s) {
         e = launch_precompute_sep<T>(all, n, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     } else if (s->solver == ADI_SOLVER_FACTORED) {
-        e = launch_fac_precompute<T>(all, n, s->stream);
+        // FP64 workspace of the dense end eliminations, one slice per line
+        DevBuf ws;
+        int rc = dev_alloc(ws, (size_t)n * fac_ws_doubles() * sizeof(double));
+        if (rc) return rc;
+        int out[2] = {0, 0};
+        e = cudaMemsetAsync(s->status.p, 0, 2 * sizeof(int), s->stream);
+        if (e == cudaSuccess) e = launch_fac_precompute<T>(all, n, (double *)ws.p, (int *)s->status.p, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->status.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        dev_free(ws);
+        if (e == cudaSuccess && out[0]) return ADI_ESINGULAR;
+        s->fac_reach = out[1];
     }
     return cuda_status(e);
 }
@@ -761,7 +778,7 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     }
     if (!rc) rc = dev_alloc(s->tab, (size_t)(g.pix + g.piy) * kTabLine * esz);
     if (!rc) rc = dev_alloc(s->clock, sizeof(long long));
-    if (!rc) rc = dev_alloc(s->status, sizeof(int));
+    if (!rc) rc = dev_alloc(s->status, 2 * sizeof(int));
     if (!rc) rc = cuda_status(cudaMemsetAsync(s->clock.p, 0, sizeof(long long), s->stream));
     if (!rc) {  // alpha = dt/2 c^2
         DevBuf staging;

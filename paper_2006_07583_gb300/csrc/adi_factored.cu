@@ -1,25 +1,37 @@
-// adi_factored.cu -- the factored line solver: persistent CTAs, line inputs staged in shared
-// memory by bulk asynchronous copies (a two-stage ring, the next line group in flight while
-// the current one is solved), chunks of a line in registers, chunks joined by segmented scans
-// of affine maps.
+// adi_factored.cu -- the factored line solver (default): persistent CTAs, whole lines staged
+// in shared memory by bulk asynchronous copies (a two-stage mbarrier ring), uniform chunks of
+// MM blocks per thread held in registers, chunks joined by segmented scans of affine maps.
 //
-// The middle system of a line (block tridiagonal, blocks A_b, B_b, C_b; head/tail already
-// eliminated, see adi_ops.cuh) has the block LU
-//     S_b = B_b - A_b G_{b-1},   G_b = S_b^{-1} C_b .
-// One thread owns a chunk of M consecutive blocks.  The FP64 precompute stores per chunk
-// only what the chunk cannot rebuild from its own data:
-//     S_{b0}   the Schur complement at the chunk's first block,
-//     F_c      prod over the chunk of F_b = -S_b^{-1} A_b   (forward transfer),
-//     H_c      prod over the chunk of -G_b                   (backward transfer).
-// Per half step a thread rebuilds S_b^{-1} of its blocks from S_{b0} and the alpha values
-// on the line (one block recurrence in the path's precision), then
-//     forward  y_b = S_b^{-1}(r_b - A_b y_{b-1})   local pass from y = 0,
-//              scan of (F_c, y_end) over the chunks -> the true y entering the chunk,
-//              correction y_b += delta_b, delta_b = F_b delta_{b-1};
-//     backward x_b = y_b - G_b x_{b+1}             local pass from x = 0,
-//              suffix scan of (H_c, x_start) -> the true x after the chunk,
-//              correction x_b += eps_b, eps_b = -G_b eps_{b+1};
-// and writes the carried outputs C = 2 u* - a (+ dt/2 f), v' = 2 v* - v.
+// Line system (adi_ops.cuh): every line is  [head region | nb middle blocks | tail region]
+// where the middle part is block tridiagonal (blocks A_b, B_b, C_b of size BS) and the two end
+// regions hold the one-sided boundary rows of App. A/B.  Here the end regions also absorb the
+// remainder of nb modulo MM, so that the middle part is exactly tact * MM blocks and every
+// thread runs the same unrolled code on MM blocks with no per-block predication.
+//
+// FP64 precompute, once per line (time invariant, depends on alpha only):
+//   * each end region is eliminated densely: its unknowns become a linear map HZ of
+//     z = [p window, v window, x of the adjacent middle block], the adjacent block's right-hand
+//     side gets the correction KZ z and its diagonal block the correction dB;
+//   * the middle part's block LU  S_b = B_b - A_b G_{b-1},  G_b = S_b^{-1} C_b  is run once and
+//     per chunk c only  S at the chunk's first block,  F_c = prod(-S_b^{-1} A_b)  and
+//     H_c = prod(-G_b)  are stored.
+// Per half step a thread rebuilds S_b^{-1} of its blocks from the stored S and the alpha values,
+// then
+//   forward   y_b = S_b^{-1}(r_b - A_b y_{b-1})  locally from y = 0; the true y entering the
+//             chunk is the exclusive scan of the maps (F_c, y_end) over the chunks; correction
+//             y_b += d_b, d_b = -S_b^{-1} A_b d_{b-1};
+//   backward  x_b = y_b - G_b x_{b+1} locally from x = 0; the true x after the chunk is the
+//             suffix scan of (H_c, x_first); correction x_b += e_b, e_b = -G_b e_{b+1};
+// and writes the carried outputs C = 2u* - a (+ dt/2 f), v' = 2v* - v.  The end regions are
+// evaluated cooperatively by the warp that owns the adjacent chunk.
+//
+// The chunk transfers decay geometrically along a line (the line systems are diagonally
+// dominant in the block sense).  The precompute finds, per line, the reach R: the smallest
+// number of consecutive chunk transfers whose product has infinity norm below tau (2^-40 for
+// FP32 records, 2^-70 for FP64).  The scan value of chunk c is then the sequential recurrence
+// over the R chunks before (after) it, read from shared memory; what it leaves out is that
+// product times a true value of the solution, i.e. below tau relative to the solution.  Lines
+// whose reach exceeds kFacMaxReach use the full log-depth scan of affine maps instead.
 #include <cuda_runtime.h>
 
 #include "adi_internal.h"
@@ -31,165 +43,170 @@ namespace adi {
 constexpr int kFacThreads = 512;              // threads per CTA
 constexpr int kFacMaxT = 512;                 // chunks (threads) per line at most
 constexpr size_t kFacSmemLimit = 227 * 1024;  // shared memory per CTA
-constexpr size_t kFacStaticSmem = 4096;       // reserve for the kernel's static shared memory
+constexpr size_t kFacStaticBase = 4096;       // reserve for the kernel's other static shared memory
+constexpr int kFacWs = 1024;                  // FP64 workspace of the precompute, per line
+constexpr int kFacMaxReach = 32;              // longest window of the windowed scans
+// Static shared memory of the kernel for element size esz: the scan buffers (chunk offsets,
+// two arrays for FP32, one for FP64) plus the rest.
+__host__ __device__ inline size_t fac_static_smem(size_t esz) {
+    return kFacStaticBase + (size_t)kFacThreads * 3 * (esz == 4 ? 2 : 1) * esz;
+}
 
-// Chunks per line (a power of two, at most kFacMaxT) and blocks per chunk.
-struct FGeom {
-    int T, M;
+// ---------------------------------------------------------------------------------------
+// Geometry of a line for the factored solver.
+// ---------------------------------------------------------------------------------------
+// Blocks per chunk: CFD 9 (an odd stride between the chunks' shared-memory windows keeps
+// their loads free of bank conflicts); MFD 2 for lines up to 2 kFacMaxT blocks, else 3.
+__host__ __device__ inline int fac_mm(int method, int N) {
+    if (method == kCFD) return 9;
+    return line_shape(kMFD, N).nb <= 2 * kFacMaxT ? 2 : 3;
+}
+// Kernel variant (one compiled instance per chunk length and method).
+__host__ __device__ inline int fac_variant_of(int method, int N) {
+    return method == kCFD ? 0 : (fac_mm(method, N) == 2 ? 1 : 2);
+}
+// End windows: p[op .. op+win) and v[ov .. ov+win); hmax bounds the eliminated unknowns of
+// one end (base head/tail plus half of at most MM-1 remainder blocks).
+__host__ __device__ inline int fac_win(int method) { return method == kCFD ? 8 : 12; }
+__host__ __device__ inline int fac_hmax(int method) { return method == kCFD ? 13 : 8; }
+
+struct FacGeom {
+    int method, N, bs, mm;
+    int hu, tu;   // eliminated unknowns of the head and tail regions
+    int nb;       // middle blocks (tact * mm)
+    int tact;     // chunks holding blocks
+    int T;        // threads per line: a power of two up to 32, else a multiple of 32
+    int first;    // CFD: node of middle block 0; MFD: first cell of middle block 0
+    int win, hmax;
 };
-__host__ __device__ inline int fac_mmax(int method) { return method == kCFD ? 8 : 3; }
-__host__ __device__ inline FGeom fgeom(int nb, int mmax) {
-    int need = (nb + mmax - 1) / mmax;
+
+__host__ __device__ inline FacGeom fac_geom(int method, int N) {
+    const LineShape s = line_shape(method, N);
+    FacGeom g;
+    g.method = method;
+    g.N = N;
+    g.bs = s.bs;
+    g.mm = fac_mm(method, N);
+    g.tact = s.nb / g.mm;
+    const int k = s.nb - g.tact * g.mm;
+    const int kh = k / 2;
+    g.hu = s.hu + kh * s.bs;
+    g.tu = s.tu + (k - kh) * s.bs;
+    g.nb = g.tact * g.mm;
     int T = 1;
-    while (T < need && T < kFacMaxT) T <<= 1;
-    FGeom g;
-    g.T = T;
-    g.M = (nb + T - 1) / T;
+    while (T < g.tact) T <<= 1;
+    g.T = g.tact > 32 ? ((g.tact + 31) & ~31) : T;
+    g.first = method == kCFD ? (g.hu + 1) / 2 : g.hu + 1;
+    g.win = fac_win(method);
+    g.hmax = fac_hmax(method);
     return g;
 }
+
+// Per-end table: KZ [bs][2win] | HZ [hmax][Z] | DZ [hmax+2][Z] (MFD) | dB [bs][bs], Z = 2win+bs.
+__host__ __device__ inline int fac_zlen(const FacGeom &g) { return 2 * g.win + g.bs; }
+__host__ __device__ inline int fac_e_hz(const FacGeom &g) { return g.bs * 2 * g.win; }
+__host__ __device__ inline int fac_e_dz(const FacGeom &g) { return fac_e_hz(g) + g.hmax * fac_zlen(g); }
+__host__ __device__ inline int fac_e_db(const FacGeom &g) {
+    return fac_e_dz(g) + (g.method == kMFD ? (g.hmax + 2) * fac_zlen(g) : 0);
+}
+__host__ __device__ inline int fac_e_stride(const FacGeom &g) { return (fac_e_db(g) + g.bs * g.bs + 3) & ~3; }
+// Record of one line: S_first, F_c, H_c (tact blocks each), the head and tail tables, then
+// four values: the forward and backward reach of the windowed scans.
+__host__ __device__ inline int fac_chunk_elems(const FacGeom &g) { return (3 * g.tact * g.bs * g.bs + 3) & ~3; }
+__host__ __device__ inline int fac_info(const FacGeom &g) { return fac_chunk_elems(g) + 2 * fac_e_stride(g); }
+__host__ __device__ inline int fac_rec(const FacGeom &g) { return fac_info(g) + 4; }
 // Elements of one staged line array (pressure, velocity or alpha), a multiple of four.
 __host__ __device__ inline int fac_lp(int N) { return (N + 2 + 3) & ~3; }
-// End tables: the head/tail eliminations and outputs as linear maps of
-//   z = [p window (8), v window (8), x of the adjacent middle block (BS)],
-// windows p[0..7], v[0..7] at the head and p[L-7..L], v[N-7..N] at the tail.  Per end:
-//   KZ [3][16]  correction of the adjacent block's right-hand side (-K W),
-//   HZ [6][19]  the eliminated unknowns (Hinv W | -Hinv E),
-//   DZ [8][19]  MFD: h (G u) at the end's velocity nodes,
-//   dB [3][3]   diagonal-block correction of the adjacent block.
-constexpr int kEndKZ = 0, kEndHZ = 48, kEndDZ = 162, kEndDB = 314;
-constexpr int kEndStride = 324, kEndTable = 2 * kEndStride;
-// Elements of one line's chunk record: S_b0, F_c, H_c as three arrays of T BSxBS blocks,
-// then the two end tables.
-__host__ __device__ inline int fac_chunk_elems(int bs, int T) { return (3 * T * bs * bs + 3) & ~3; }
-__host__ __device__ inline int fac_rec(int bs, int T) { return fac_chunk_elems(bs, T) + kEndTable; }
-__host__ __device__ inline FGeom fac_geom(int method, int N) {
-    return fgeom(line_shape(method, N).nb, fac_mmax(method));
-}
-__host__ __device__ inline int fac_line_elems(int method, int N) {
-    LineShape s = line_shape(method, N);
-    return 3 * fac_lp(N) + fac_rec(s.bs, fac_geom(method, N).T);
-}
+__host__ __device__ inline int fac_line_elems(const FacGeom &g) { return 3 * fac_lp(g.N) + fac_rec(g); }
 
-// One stage: the group's descriptors, then per line [p | v | alpha | record].
 constexpr size_t kDescBytes = sizeof(LineDesc<float>);
 static_assert(sizeof(LineDesc<float>) == sizeof(LineDesc<double>), "descriptor sizes differ");
 static_assert(kDescBytes % 16 == 0, "descriptor size");
 __host__ __device__ inline size_t fac_desc_area(int nl) { return ((size_t)nl * kDescBytes + 127) & ~(size_t)127; }
+
 size_t fac_stage_bytes(int method, int N, int nl, size_t esz) {
-    size_t b = fac_desc_area(nl) + (size_t)nl * fac_line_elems(method, N) * esz;
+    size_t b = fac_desc_area(nl) + (size_t)nl * fac_line_elems(fac_geom(method, N)) * esz;
     return (b + 127) & ~(size_t)127;
 }
-int fac_stages_for(size_t stage_bytes) {
-    if (2 * stage_bytes + kFacStaticSmem <= kFacSmemLimit) return 2;
-    if (stage_bytes + kFacStaticSmem <= kFacSmemLimit) return 1;
+int fac_stages_for(size_t stage_bytes, size_t esz) {
+    if (2 * stage_bytes + fac_static_smem(esz) <= kFacSmemLimit) return 2;
+    if (stage_bytes + fac_static_smem(esz) <= kFacSmemLimit) return 1;
     return 0;
 }
 // Lines per CTA: as many as the CTA's threads cover, fewer where a two-stage ring of them
 // would not fit shared memory.
 int fac_lines_per_cta(int method, int N, size_t esz) {
-    int T = fac_geom(method, N).T;
+    const int T = fac_geom(method, N).T;
     int nl = T >= kFacThreads ? 1 : kFacThreads / T;
-    while (nl > 1 && fac_stages_for(fac_stage_bytes(method, N, nl, esz)) < 2) --nl;
+    while (nl > 1 && fac_stages_for(fac_stage_bytes(method, N, nl, esz), esz) < 2) --nl;
     return nl;
 }
 bool fac_supported(int method, int N, size_t esz) {
-    if (fac_geom(method, N).M > fac_mmax(method)) return false;
-    return fac_stages_for(fac_stage_bytes(method, N, 1, esz)) > 0;
+    const FacGeom g = fac_geom(method, N);
+    if (g.tact < 1 || g.T > kFacMaxT) return false;
+    if (g.hu > g.hmax || g.tu > g.hmax) return false;
+    return fac_stages_for(fac_stage_bytes(method, N, 1, esz), esz) > 0;
 }
-size_t fac_words(int method, int N) {
-    return (size_t)fac_rec(line_shape(method, N).bs, fac_geom(method, N).T);
-}
+size_t fac_words(int method, int N) { return (size_t)fac_rec(fac_geom(method, N)); }
 int fac_chunks(int method, int N) { return fac_geom(method, N).T; }
+int fac_variant(int method, int N) { return fac_variant_of(method, N); }
+size_t fac_ws_doubles() { return kFacWs; }
 
 // ---------------------------------------------------------------------------------------
-// Small block helpers.
+// Middle block b (A to block b-1, B, C to block b+1) in precision R from alpha values
+// al(k) along the pressure line.
 // ---------------------------------------------------------------------------------------
-template <typename T, int BS>
-__device__ __forceinline__ void f_mm(const T (&X)[BS][BS], const T (&Y)[BS][BS], T (&R)[BS][BS]) {
+template <typename R, int BS, typename AL>
+__device__ __forceinline__ void fac_block(const FacGeom &g, double beta, double ih, int b, AL al,
+                                          R (&A)[BS][BS], R (&B)[BS][BS], R (&C)[BS][BS]) {
+    if constexpr (BS == 2) {
+        const int j = g.first + b;
+        const R tb = R(3) * (R)beta * (R)ih;
+        A[0][0] = R(1); A[0][1] = -tb; A[1][0] = -R(3) * (R)ih * (R)al(j - 1); A[1][1] = R(1);
+        B[0][0] = R(4); B[0][1] = R(0); B[1][0] = R(0); B[1][1] = R(4);
+        C[0][0] = R(1); C[0][1] = tb; C[1][0] = R(3) * (R)ih * (R)al(j + 1); C[1][1] = R(1);
+    } else {
+        const int cb = g.first + 3 * b;
+        const R bh2 = (R)(beta * ih * ih);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const R sc = (R)al(cb + m) * bh2;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                A[m][q] = (q >= m) ? -sc * (R)mim_DG(q - m) : R(0);
+                B[m][q] = (q == m ? R(1) : R(0)) - sc * (R)mim_DG(q - m + 3);
+                C[m][q] = (q <= m) ? -sc * (R)mim_DG(q - m + 6) : R(0);
+            }
+        }
+    }
+}
+
+template <typename R, int BS>
+__device__ __forceinline__ void f_mm(const R (&X)[BS][BS], const R (&Y)[BS][BS], R (&Z)[BS][BS]) {
 #pragma unroll
     for (int i = 0; i < BS; ++i)
 #pragma unroll
         for (int j = 0; j < BS; ++j) {
-            T acc = T(0);
+            R acc = R(0);
 #pragma unroll
             for (int k = 0; k < BS; ++k) acc += X[i][k] * Y[k][j];
-            R[i][j] = acc;
+            Z[i][j] = acc;
         }
 }
 
 // ---------------------------------------------------------------------------------------
-// FP64 precompute of the chunk records, one thread per line.
+// FP64 precompute.
 // ---------------------------------------------------------------------------------------
-template <typename TS, int BS>
-__device__ void fac_precompute_line(const LineDesc<TS> &d, TS *rec) {
-    const Line<TS> L(d);
-    const LineShape s = line_shape(d.method, d.N);
-    const FGeom g = fgeom(s.nb, fac_mmax(d.method));
-    const double rz[6] = {0, 0, 0, 0, 0, 0};
-    constexpr int B2 = BS * BS;
-    TS *recS = rec, *recF = rec + (size_t)g.T * B2, *recH = rec + (size_t)2 * g.T * B2;
-    double G[BS][BS], Fp[BS][BS], Hp[BS][BS];
-    for (int p = 0; p < BS; ++p)
-        for (int q = 0; q < BS; ++q) { G[p][q] = 0.0; Fp[p][q] = Hp[p][q] = (p == q) ? 1.0 : 0.0; }
-    for (int b = 0; b < s.nb; ++b) {
-        double A[BS][BS], B[BS][BS], C[BS][BS], r[BS];
-        load_block<double, TS, BS>(L, s, b, rz, rz, A, B, C, r);
-        double S[BS][BS], Si[BS][BS], Gn[BS][BS], Fb[BS][BS], T1[BS][BS];
-        for (int p = 0; p < BS; ++p)
-            for (int q = 0; q < BS; ++q) {
-                double acc = B[p][q];
-                for (int k = 0; k < BS; ++k) acc -= A[p][k] * G[k][q];
-                S[p][q] = acc;
-            }
-        mat_inv<double, BS>(S, Si);
-        f_mm<double, BS>(Si, C, Gn);
-        f_mm<double, BS>(Si, A, Fb);
-        const int c = b / g.M, i = b % g.M;
-        if (i == 0) {
-            for (int p = 0; p < BS; ++p)
-                for (int q = 0; q < BS; ++q) {
-                    recS[(size_t)c * B2 + p * BS + q] = (TS)S[p][q];
-                    Fp[p][q] = Hp[p][q] = (p == q) ? 1.0 : 0.0;
-                }
-        }
-        // Fp <- (-Si A) Fp ;  Hp <- Hp (-Gn)
-        f_mm<double, BS>(Fb, Fp, T1);
-        for (int p = 0; p < BS; ++p)
-            for (int q = 0; q < BS; ++q) Fp[p][q] = -T1[p][q];
-        f_mm<double, BS>(Hp, Gn, T1);
-        for (int p = 0; p < BS; ++p)
-            for (int q = 0; q < BS; ++q) Hp[p][q] = -T1[p][q];
-        if (i == g.M - 1 || b == s.nb - 1) {
-            for (int p = 0; p < BS; ++p)
-                for (int q = 0; q < BS; ++q) {
-                    recF[(size_t)c * B2 + p * BS + q] = (TS)Fp[p][q];
-                    recH[(size_t)c * B2 + p * BS + q] = (TS)Hp[p][q];
-                }
-        }
-        for (int p = 0; p < BS; ++p)
-            for (int q = 0; q < BS; ++q) G[p][q] = Gn[p][q];
-    }
-    // chunks past the end of the line act as identities
-    for (int c = (s.nb + g.M - 1) / g.M; c < g.T; ++c)
-        for (int p = 0; p < BS; ++p)
-            for (int q = 0; q < BS; ++q) {
-                const TS e = (TS)(p == q ? 1.0 : 0.0);
-                recS[(size_t)c * B2 + p * BS + q] = e;
-                recF[(size_t)c * B2 + p * BS + q] = e;
-                recH[(size_t)c * B2 + p * BS + q] = e;
-            }
-}
-
-// Right-hand side of head/tail row i as coefficients on the windows p[op..op+7] and
-// v[ov..ov+7] (the same sums rhs_row evaluates).  False if a term falls outside.
+// Right-hand side of line row i (solver index) as coefficients on the windows
+// p[op .. op+W) and v[ov .. ov+W).  False if a term falls outside them.
 template <typename TS>
-__device__ bool rhs_coeffs(const LineDesc<TS> &d, int i, int op, int ov, double (&cp)[8], double (&cv)[8]) {
-    for (int k = 0; k < 8; ++k) cp[k] = cv[k] = 0.0;
+__device__ bool fac_rhs_coeffs(const LineDesc<TS> &d, int i, int op, int ov, int W, double *cp, double *cv) {
+    for (int k = 0; k < W; ++k) cp[k] = cv[k] = 0.0;
     const int N = d.N;
     const double ih = d.inv_h;
     bool ok = true;
-    auto add = [&](double (&w8)[8], int idx, double val) {
-        if (idx < 0 || idx >= 8) ok = false; else w8[idx] += val;
+    auto add = [&](double *w, int idx, double val) {
+        if (idx < 0 || idx >= W) ok = false; else w[idx] += val;
     };
     double w[8];
     int c0, n;
@@ -205,7 +222,7 @@ __device__ bool rhs_coeffs(const LineDesc<TS> &d, int i, int op, int ov, double 
         }
         return ok;
     }
-    // r_c = p_c - alpha_c/h sum_j D[c-1][j] (v_j - beta/h (G[j][0] p_0 + G[j][N+1] p_L))
+    // r_c = p_c - alpha_c/h sum_j D[c-1][j] (v_j - beta/h (G[j][0] p_0 + G[j][N+1] p_{N+1}))
     const int c = i + 1;
     const double a = (double)d.alpha[(long long)c * d.sp], bh = d.beta * ih;
     add(cp, c - op, 1.0);
@@ -225,94 +242,223 @@ __device__ bool rhs_coeffs(const LineDesc<TS> &d, int i, int op, int ov, double 
     return ok;
 }
 
-// The two end tables of a line (see kEnd*), from the head/tail elimination tables.
-template <typename TS, int BS>
-__device__ void fac_end_tables(const LineDesc<TS> &d, TS *et) {
-    const int N = d.N;
-    const LineShape s = line_shape(d.method, N);
+// Dense elimination of one end region (end 0: head, 1: tail) into its table; dB of the end
+// (bs x bs, row-major) is also returned in dBo.  False if the region is singular.
+template <typename TS>
+__device__ bool fac_end(const LineDesc<TS> &d, const FacGeom &g, int end, double *ws, TS *et, double *dBo) {
+    const int N = d.N, bs = g.bs, W = g.win, Z = fac_zlen(g);
+    const int nunk = d.method == kCFD ? 2 * N : N;
+    const int m = end == 0 ? g.hu : g.tu;
+    const int r0 = end == 0 ? 0 : nunk - g.tu;
+    const int j0 = end == 0 ? g.hu : nunk - g.tu - bs;
     const int pl = p_last(d.method, N);
+    const int op = end == 0 ? 0 : pl + 1 - W, ov = end == 0 ? 0 : N + 1 - W;
+    double *H = ws, *Hi = H + m * m, *E = Hi + m * m, *F = E + m * bs, *Rm = F + bs * m;
+    double *HiE = Rm + m * 2 * W, *K = HiE + m * bs, *HZ = K + bs * m;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) H[i * m + j] = line_entry(d, r0 + i, r0 + j);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < bs; ++j) E[i * bs + j] = line_entry(d, r0 + i, j0 + j);
+    for (int i = 0; i < bs; ++i)
+        for (int j = 0; j < m; ++j) F[i * m + j] = line_entry(d, j0 + i, r0 + j);
+    if (!small_inverse(H, m, Hi)) return false;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < bs; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < m; ++k) acc += Hi[i * m + k] * E[k * bs + j];
+            HiE[i * bs + j] = acc;
+        }
+    for (int i = 0; i < bs; ++i)
+        for (int j = 0; j < m; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < m; ++k) acc += F[i * m + k] * Hi[k * m + j];
+            K[i * m + j] = acc;
+        }
+    for (int i = 0; i < bs; ++i)
+        for (int j = 0; j < bs; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < m; ++k) acc += F[i * m + k] * HiE[k * bs + j];
+            dBo[i * bs + j] = acc;
+        }
+    bool ok = true;
+    for (int q = 0; q < m; ++q) ok = fac_rhs_coeffs(d, r0 + q, op, ov, W, Rm + q * 2 * W, Rm + q * 2 * W + W) && ok;
     const double nan = __longlong_as_double(0x7ff8000000000000ULL);
-    for (int end = 0; end < 2; ++end) {
-        TS *e = et + end * kEndStride;
-        const TS *t = d.tab + end * kTabEnd;
-        const int m = end == 0 ? s.hu : s.tu;
-        const int r0 = end == 0 ? 0 : s.nunk - s.tu;
-        const int op = end == 0 ? 0 : pl - 7, ov = end == 0 ? 0 : N - 7;
-        double W[6][16];
-        bool ok = true;
-        for (int k = 0; k < m; ++k) {
-            double cp[8], cv[8];
-            ok = rhs_coeffs(d, r0 + k, op, ov, cp, cv) && ok;
-            for (int j = 0; j < 8; ++j) { W[k][j] = cp[j]; W[k][8 + j] = cv[j]; }
+    const int e_stride = fac_e_stride(g);
+    for (int i = 0; i < e_stride; ++i) et[i] = (TS)0;
+    // KZ = -K R
+    for (int p = 0; p < bs; ++p)
+        for (int k = 0; k < 2 * W; ++k) {
+            double acc = 0.0;
+            for (int q = 0; q < m; ++q) acc -= K[p * m + q] * Rm[q * 2 * W + k];
+            et[p * 2 * W + k] = (TS)(ok ? acc : nan);
         }
-        for (int i = 0; i < kEndStride; ++i) e[i] = (TS)0;
-        for (int p = 0; p < BS; ++p)
-            for (int j = 0; j < 16; ++j) {
-                double acc = 0.0;
-                for (int k = 0; k < m; ++k) acc -= (double)t[kTabK + p * m + k] * W[k][j];
-                e[kEndKZ + p * 16 + j] = (TS)(ok ? acc : nan);
-            }
-        double HZ[6][19];
-        for (int q = 0; q < m; ++q) {
-            for (int j = 0; j < 16; ++j) {
-                double acc = 0.0;
-                for (int k = 0; k < m; ++k) acc += (double)t[kTabHinv + q * m + k] * W[k][j];
-                HZ[q][j] = acc;
-            }
-            for (int b = 0; b < 3; ++b) HZ[q][16 + b] = b < BS ? -(double)t[kTabHinvE + q * BS + b] : 0.0;
-            for (int j = 0; j < 19; ++j) e[kEndHZ + q * 19 + j] = (TS)(ok ? HZ[q][j] : nan);
+    // HZ = [Hinv R | -Hinv E]
+    for (int q = 0; q < m; ++q) {
+        for (int k = 0; k < 2 * W; ++k) {
+            double acc = 0.0;
+            for (int q2 = 0; q2 < m; ++q2) acc += Hi[q * m + q2] * Rm[q2 * 2 * W + k];
+            HZ[q * Z + k] = acc;
         }
-        for (int p = 0; p < BS; ++p)
-            for (int q = 0; q < BS; ++q) e[kEndDB + p * 3 + q] = t[kTabDB + p * BS + q];
-        if (d.method != kMFD) continue;
-        // MFD: h (G u)_j at the end's nodes, cells expressed through z
-        const int qb = s.hu + 1 + 3 * (s.nb - 1);  // first cell of the last middle block
-        const int j0 = end == 0 ? 0 : qb + 1, j1 = end == 0 ? s.hu + 1 : N;
-        for (int j = j0; j <= j1; ++j) {
-            double row[19];
-            for (int k = 0; k < 19; ++k) row[k] = 0.0;
-            double gw[8];
-            int g0;
-            const int ng = mfd_G_row(N, j, &g0, gw);
-            bool rok = ok;
-            for (int tt = 0; tt < ng; ++tt) {
-                const int cc = g0 + tt;
-                if (end == 0) {
-                    if (cc == 0) row[0] += gw[tt];
-                    else if (cc <= s.hu) for (int k = 0; k < 19; ++k) row[k] += gw[tt] * HZ[cc - 1][k];
-                    else if (cc <= s.hu + 3) row[16 + cc - s.hu - 1] += gw[tt];
-                    else rok = false;
-                } else {
-                    if (cc == N + 1) row[N + 1 - op] += gw[tt];
-                    else if (cc >= qb + 3) for (int k = 0; k < 19; ++k) row[k] += gw[tt] * HZ[cc - qb - 3][k];
-                    else if (cc >= qb) row[16 + cc - qb] += gw[tt];
-                    else rok = false;
-                }
-            }
-            for (int k = 0; k < 19; ++k) e[kEndDZ + (j - j0) * 19 + k] = (TS)(rok ? row[k] : nan);
-        }
+        for (int b = 0; b < bs; ++b) HZ[q * Z + 2 * W + b] = -HiE[q * bs + b];
+        for (int k = 0; k < Z; ++k) et[fac_e_hz(g) + q * Z + k] = (TS)(ok ? HZ[q * Z + k] : nan);
     }
+    for (int i = 0; i < bs * bs; ++i) et[fac_e_db(g) + i] = (TS)dBo[i];
+    if (d.method != kMFD) return true;
+    // MFD: h (G u)_j at the end's velocity nodes as maps of z (cells through HZ)
+    const int qb = g.first + 3 * (g.nb - 1);  // first cell of the last middle block
+    const int jlo = end == 0 ? 0 : qb + 1, jhi = end == 0 ? g.hu + 1 : N;
+    const int cell_lo = end == 0 ? 1 : N - g.tu + 1;  // first eliminated cell
+    const int adj = end == 0 ? g.hu + 1 : qb;         // first cell of the adjacent block
+    for (int j = jlo; j <= jhi; ++j) {
+        double *row = HZ + m * Z;  // scratch row after HZ
+        for (int k = 0; k < Z; ++k) row[k] = 0.0;
+        double gw[8];
+        int g0;
+        const int ng = mfd_G_row(N, j, &g0, gw);
+        bool rok = ok;
+        for (int t = 0; t < ng; ++t) {
+            const int cc = g0 + t;
+            if (cc == 0 || cc == N + 1) {
+                const int wi = cc - op;
+                if (wi < 0 || wi >= W) rok = false; else row[wi] += gw[t];
+            } else if (cc >= cell_lo && cc < cell_lo + m) {
+                for (int k = 0; k < Z; ++k) row[k] += gw[t] * HZ[(cc - cell_lo) * Z + k];
+            } else if (cc >= adj && cc < adj + bs) {
+                row[2 * W + cc - adj] += gw[t];
+            } else {
+                rok = false;
+            }
+        }
+        for (int k = 0; k < Z; ++k) et[fac_e_dz(g) + (j - jlo) * Z + k] = (TS)(rok ? row[k] : nan);
+    }
+    return true;
+}
+
+template <typename TS, int BS>
+__device__ bool fac_chunks_fp64(const LineDesc<TS> &d, const FacGeom &g, const double *dBh, const double *dBt, TS *rec) {
+    constexpr int B2 = BS * BS;
+    TS *recS = rec, *recF = rec + (size_t)g.tact * B2, *recH = rec + (size_t)2 * g.tact * B2;
+    auto al = [&](int k) -> double { return (double)d.alpha[(long long)k * d.sp]; };
+    double G[BS][BS], Fp[BS][BS], Hp[BS][BS];
+    for (int p = 0; p < BS; ++p)
+        for (int q = 0; q < BS; ++q) { G[p][q] = 0.0; Fp[p][q] = Hp[p][q] = (p == q) ? 1.0 : 0.0; }
+    for (int b = 0; b < g.nb; ++b) {
+        double A[BS][BS], B[BS][BS], C[BS][BS];
+        fac_block<double, BS>(g, d.beta, d.inv_h, b, al, A, B, C);
+        if (b == 0)
+            for (int p = 0; p < BS; ++p)
+                for (int q = 0; q < BS; ++q) { B[p][q] -= dBh[p * BS + q]; A[p][q] = 0.0; }
+        if (b == g.nb - 1)
+            for (int p = 0; p < BS; ++p)
+                for (int q = 0; q < BS; ++q) { B[p][q] -= dBt[p * BS + q]; C[p][q] = 0.0; }
+        double S[BS][BS], Si[BS][BS], Gn[BS][BS], T1[BS][BS];
+        for (int p = 0; p < BS; ++p)
+            for (int q = 0; q < BS; ++q) {
+                double acc = B[p][q];
+                for (int k = 0; k < BS; ++k) acc -= A[p][k] * G[k][q];
+                S[p][q] = acc;
+            }
+        double det = BS == 2 ? S[0][0] * S[1][1] - S[0][1] * S[1][0]
+                             : S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
+                                   S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
+                                   S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
+        if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
+        mat_inv<double, BS>(S, Si);
+        f_mm<double, BS>(Si, C, Gn);
+        const int c = b / g.mm, i = b % g.mm;
+        if (i == 0) {
+            for (int p = 0; p < BS; ++p)
+                for (int q = 0; q < BS; ++q) {
+                    recS[(size_t)c * B2 + p * BS + q] = (TS)S[p][q];
+                    Fp[p][q] = Hp[p][q] = (p == q) ? 1.0 : 0.0;
+                }
+        }
+        // Fp <- (-Si A) Fp ;  Hp <- Hp (-Gn)
+        double Fb[BS][BS];
+        f_mm<double, BS>(Si, A, Fb);
+        f_mm<double, BS>(Fb, Fp, T1);
+        for (int p = 0; p < BS; ++p)
+            for (int q = 0; q < BS; ++q) Fp[p][q] = -T1[p][q];
+        f_mm<double, BS>(Hp, Gn, T1);
+        for (int p = 0; p < BS; ++p)
+            for (int q = 0; q < BS; ++q) Hp[p][q] = -T1[p][q];
+        if (i == g.mm - 1)
+            for (int p = 0; p < BS; ++p)
+                for (int q = 0; q < BS; ++q) {
+                    recF[(size_t)c * B2 + p * BS + q] = (TS)Fp[p][q];
+                    recH[(size_t)c * B2 + p * BS + q] = (TS)Hp[p][q];
+                }
+        for (int p = 0; p < BS; ++p)
+            for (int q = 0; q < BS; ++q) G[p][q] = Gn[p][q];
+    }
+    return true;
+}
+
+// Reach of the windowed scans (see the header): the largest, over the chunks, of the number
+// of consecutive stored transfers (forward: F_e F_{e-1} ..., backward: H_s H_{s+1} ...) whose
+// product first has infinity norm at most tau, or that reaches the end of the line; at most
+// kFacMaxReach + 1 (which selects the full scan).
+template <typename TS, int BS>
+__device__ int fac_reach(const TS *maps, int tact, double tau, bool forward) {
+    constexpr int B2 = BS * BS;
+    int reach = 0;
+    for (int e = 0; e < tact - 1; ++e) {
+        const int first = forward ? e : e + 1;  // chunk whose transfer the window starts with
+        double P[BS][BS];
+        for (int p = 0; p < BS; ++p)
+            for (int q = 0; q < BS; ++q) P[p][q] = p == q ? 1.0 : 0.0;
+        int r = 0;
+        for (;;) {
+            const int k = forward ? first - r : first + r;
+            double M[BS][BS], T1[BS][BS];
+            for (int p = 0; p < BS; ++p)
+                for (int q = 0; q < BS; ++q) M[p][q] = (double)maps[(size_t)k * B2 + p * BS + q];
+            f_mm<double, BS>(P, M, T1);
+            double nrm = 0.0;
+            for (int p = 0; p < BS; ++p) {
+                double rs = 0.0;
+                for (int q = 0; q < BS; ++q) { P[p][q] = T1[p][q]; rs += fabs(T1[p][q]); }
+                nrm = fmax(nrm, rs);
+            }
+            ++r;
+            const bool at_end = forward ? (k == 0) : (k == tact - 1);
+            if (nrm <= tau || at_end || r > kFacMaxReach) break;
+        }
+        reach = max(reach, r);
+        if (reach > kFacMaxReach) break;
+    }
+    return reach;
 }
 
 template <typename TS>
-__global__ void fac_precompute_kernel(const LineDesc<TS> *__restrict__ descs, int nlines) {
-    int line = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void fac_precompute_kernel(const LineDesc<TS> *__restrict__ descs, int nlines, double *ws,
+                                      int *status) {
+    const int line = blockIdx.x * blockDim.x + threadIdx.x;
     if (line >= nlines) return;
     const LineDesc<TS> d = descs[line];
-    const LineShape s = line_shape(d.method, d.N);
-    TS *et = d.sep + fac_chunk_elems(s.bs, fac_geom(d.method, d.N).T);
-    if (d.method == kCFD) {
-        fac_precompute_line<TS, 2>(d, d.sep);
-        fac_end_tables<TS, 2>(d, et);
-    } else {
-        fac_precompute_line<TS, 3>(d, d.sep);
-        fac_end_tables<TS, 3>(d, et);
-    }
+    const FacGeom g = fac_geom(d.method, d.N);
+    double *w = ws + (size_t)line * kFacWs;
+    TS *rec = d.sep;
+    TS *eH = rec + fac_chunk_elems(g), *eT = eH + fac_e_stride(g);
+    double dBh[9], dBt[9];
+    bool ok = fac_end(d, g, 0, w, eH, dBh) && fac_end(d, g, 1, w, eT, dBt);
+    if (ok) ok = d.method == kCFD ? fac_chunks_fp64<TS, 2>(d, g, dBh, dBt, rec)
+                                  : fac_chunks_fp64<TS, 3>(d, g, dBh, dBt, rec);
+    if (!ok) { atomicExch(status, 1); return; }
+    const double tau = sizeof(TS) == 4 ? 0x1p-40 : 0x1p-70;
+    const int B2 = g.bs * g.bs;
+    const TS *F = rec + (size_t)g.tact * B2, *H = rec + (size_t)2 * g.tact * B2;
+    const int rf = d.method == kCFD ? fac_reach<TS, 2>(F, g.tact, tau, true) : fac_reach<TS, 3>(F, g.tact, tau, true);
+    const int rb = d.method == kCFD ? fac_reach<TS, 2>(H, g.tact, tau, false) : fac_reach<TS, 3>(H, g.tact, tau, false);
+    TS *info = rec + fac_info(g);
+    info[0] = (TS)rf;
+    info[1] = (TS)rb;
+    info[2] = info[3] = (TS)0;
+    atomicMax(status + 1, max(rf, rb));
 }
 
 // ---------------------------------------------------------------------------------------
-// Segmented scans of affine maps z -> m z + off over the T chunk-threads of a line.
-// Lines occupy aligned groups of T consecutive threads (T a power of two).
+// Affine maps z -> m z + off and their segmented scans over the chunks of a line.
 // ---------------------------------------------------------------------------------------
 template <typename T, int BS>
 struct Map {
@@ -349,8 +495,7 @@ __device__ __forceinline__ void map_after(Map<T, BS> &a, const Map<T, BS> &b) {
     a = r;
 }
 template <typename T, int BS>
-__device__ __forceinline__ void map_shfl(Map<T, BS> &dst, const Map<T, BS> &src, int delta, bool up,
-                                         int width) {
+__device__ __forceinline__ void map_shfl(Map<T, BS> &dst, const Map<T, BS> &src, int delta, bool up, int width) {
 #pragma unroll
     for (int i = 0; i < BS; ++i) {
 #pragma unroll
@@ -362,18 +507,24 @@ __device__ __forceinline__ void map_shfl(Map<T, BS> &dst, const Map<T, BS> &src,
     }
 }
 
-// Inclusive scan over the chunks of a line.  forward: result(c) = a_c o ... o a_0;
-// backward: result(c) = a_c o a_{c+1} o ... o a_{T-1}.  Returns the exclusive value's
-// offset applied to zero, i.e. z before chunk c (forward) or after chunk c (backward).
-// sm holds 32 maps (warp aggregates, then warp prefixes); all threads of the CTA must
-// call it.
+// Scan buffers of a CTA: warp aggregates and warp prefixes.
 template <typename T, int BS>
-__device__ void line_scan(Map<T, BS> a, bool forward, int Tl, T (&z)[BS], Map<T, BS> *sm) {
+struct ScanSmem {
+    Map<T, BS> agg[kFacThreads / 32];
+    T pre[kFacThreads / 32][BS];
+};
+
+// Exclusive scan over the Tl chunk-threads of each line (lines occupy aligned groups of Tl
+// consecutive threads; threads past the last whole line of the CTA take part in the warp
+// shuffles only).  forward: z(c) = (a_{c-1} o ... o a_0)(0), the value entering chunk c;
+// backward: z(c) = (a_{c+1} o ... o a_{Tl-1})(0), the value after chunk c.  Every thread of
+// the CTA must call it with the same Tl.
+template <typename T, int BS>
+__device__ __forceinline__ void seg_scan(Map<T, BS> a, bool forward, int Tl, T (&z)[BS], ScanSmem<T, BS> &sm) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int width = Tl < 32 ? Tl : 32;
     const int pos = forward ? (lane % width) : (width - 1 - lane % width);
-    // warp-level (segment width <= 32) inclusive scan
 #pragma unroll
     for (int s = 1; s < 32; s <<= 1) {
         if (s >= width) break;
@@ -381,55 +532,48 @@ __device__ void line_scan(Map<T, BS> a, bool forward, int Tl, T (&z)[BS], Map<T,
         map_shfl<T, BS>(o, a, s, forward, width);
         if (pos >= s) map_after<T, BS>(a, o);
     }
-    T zz[BS];
-    // exclusive value within the warp segment
+    Map<T, BS> ex;
+    map_shfl<T, BS>(ex, a, 1, forward, width);
+    if (pos == 0) map_id<T, BS>(ex);
+    if (Tl <= 32) {
+#pragma unroll
+        for (int i = 0; i < BS; ++i) z[i] = ex.off[i];
+        return;
+    }
+    const int nw = Tl >> 5;          // warps per line
+    const int wl = warp % nw;        // warp index within its line
+    const bool whole = (tid / Tl) < (int)(blockDim.x / Tl);  // inside a whole line of the CTA
+    if (pos == 31) sm.agg[warp] = a;  // the warp's full composition
+    __syncthreads();
+    if (whole && wl == 0 && lane == 0) {
+        T p[BS];
+#pragma unroll
+        for (int i = 0; i < BS; ++i) p[i] = T(0);
+        for (int k = 0; k < nw; ++k) {
+            const int w = warp + (forward ? k : nw - 1 - k);
+#pragma unroll
+            for (int i = 0; i < BS; ++i) sm.pre[w][i] = p[i];
+            const Map<T, BS> &ag = sm.agg[w];
+            T q[BS];
+#pragma unroll
+            for (int i = 0; i < BS; ++i) {
+                T acc = ag.off[i];
+#pragma unroll
+                for (int k2 = 0; k2 < BS; ++k2) acc += ag.m[i][k2] * p[k2];
+                q[i] = acc;
+            }
+#pragma unroll
+            for (int i = 0; i < BS; ++i) p[i] = q[i];
+        }
+    }
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < BS; ++i) {
-        T v = forward ? __shfl_up_sync(0xffffffffu, a.off[i], 1, width)
-                      : __shfl_down_sync(0xffffffffu, a.off[i], 1, width);
-        zz[i] = pos == 0 ? T(0) : v;
+        T acc = ex.off[i];
+#pragma unroll
+        for (int k = 0; k < BS; ++k) acc += ex.m[i][k] * sm.pre[warp][k];
+        z[i] = acc;
     }
-    if (Tl > 32) {
-        // combine the warps of a line: warp aggregates go to shared memory, the first warp of
-        // each line scans them (exclusive), every warp applies its prefix
-        const int wpl = Tl / 32;              // warps per line (<= 16)
-        const int wl = warp % wpl;            // warp index within its line
-        const int wfirst = warp - wl;
-        const int last_lane = forward ? 31 : 0;
-        if (lane == last_lane) sm[warp] = a;  // the warp's full composition
-        __syncthreads();
-        if (wl == 0) {
-            // lane t < wpl holds warp aggregate t; scan across them (width = wpl)
-            Map<T, BS> w;
-            if (lane < wpl) w = sm[wfirst + lane]; else map_id<T, BS>(w);
-            const int wpos = forward ? lane : (wpl - 1 - lane);
-#pragma unroll
-            for (int s2 = 1; s2 < 16; s2 <<= 1) {
-                if (s2 >= wpl) break;
-                Map<T, BS> o;
-                map_shfl<T, BS>(o, w, s2, forward, 32);
-                if (lane < wpl && wpos >= s2) map_after<T, BS>(w, o);
-            }
-            // exclusive prefix for warp `lane`
-            Map<T, BS> ex;
-            map_shfl<T, BS>(ex, w, 1, forward, 32);
-            if (wpos == 0) map_id<T, BS>(ex);
-            __syncwarp();
-            if (lane < wpl) sm[16 + wfirst + lane] = ex;
-        }
-        __syncthreads();
-        const Map<T, BS> pre = sm[16 + warp];
-        // z = (exclusive within warp) o pre, applied to zero
-        Map<T, BS> ex;
-        map_shfl<T, BS>(ex, a, 1, forward, 32);
-        if (pos == 0) map_id<T, BS>(ex);
-        map_after<T, BS>(ex, pre);
-#pragma unroll
-        for (int i = 0; i < BS; ++i) zz[i] = ex.off[i];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < BS; ++i) z[i] = zz[i];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -445,12 +589,10 @@ __device__ __forceinline__ void mbar_fence_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigned bytes,
-                                             unsigned long long *bar) {
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_addr(dst)),
@@ -478,20 +620,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 
 __host__ __device__ inline unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
 
-// Thread 0: stage the inputs of one line group (pressure, velocity and alpha lines and the
-// chunk records) into shared memory.  Every source line starts on a 16-byte boundary (the
-// carried arrays have padded leading dimensions) and the copies, rounded up to 16 bytes,
-// stay inside the padded line.
+// Thread 0: stage one line group (descriptors, then per line the pressure, velocity and alpha
+// lines and the record) into shared memory.  Every source line starts on a 16-byte boundary
+// (padded leading dimensions) and the copies, rounded up to 16 bytes, stay inside the padded
+// line.
 template <typename T>
 __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, int4 gr, unsigned char *stage,
                           unsigned long long *bar) {
     const LineDesc<T> &d0 = descs[gr.x];
-    const int N = d0.N, method = d0.method;
-    const LineShape s = line_shape(method, N);
-    const FGeom g = fgeom(s.nb, fac_mmax(method));
-    const int Lp = fac_lp(N), R = fac_rec(s.bs, g.T);
-    const unsigned bp = round16((unsigned)(p_last(method, N) + 1) * (unsigned)sizeof(T));
-    const unsigned bv = round16((unsigned)(N + 1) * (unsigned)sizeof(T));
+    const FacGeom g = fac_geom(d0.method, d0.N);
+    const int Lp = fac_lp(g.N), R = fac_rec(g);
+    const unsigned bp = round16((unsigned)(p_last(g.method, g.N) + 1) * (unsigned)sizeof(T));
+    const unsigned bv = round16((unsigned)(g.N + 1) * (unsigned)sizeof(T));
     const unsigned br = (unsigned)R * (unsigned)sizeof(T);
     const unsigned bd = (unsigned)(gr.y * kDescBytes);
     mbar_expect_tx(bar, bd + (unsigned)gr.y * (2 * bp + bv + br));
@@ -507,150 +647,176 @@ __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, int4 gr, unsign
     }
 }
 
-// W consecutive elements of shared memory into registers: 16-byte loads where src is
-// 16-byte aligned, element loads otherwise.
+// W consecutive shared-memory elements into registers (8-byte loads for float when the
+// source is 8-byte aligned).
 template <typename T, int W>
-__device__ __forceinline__ void load_window(const T *src, T (&w)[W]) {
-    constexpr int per = 16 / (int)sizeof(T);
-    static_assert(W % per == 0, "window");
-    if ((smem_addr(src) & 15u) == 0) {
+__device__ __forceinline__ void load_win(const T *src, T (&w)[W]) {
+    if constexpr (sizeof(T) == 4 && W % 2 == 0) {
+        if ((smem_addr(src) & 7u) == 0) {
 #pragma unroll
-        for (int k = 0; k < W; k += per) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(src + k);
-            const T *e = reinterpret_cast<const T *>(&q);
-#pragma unroll
-            for (int j = 0; j < per; ++j) w[k + j] = e[j];
+            for (int k = 0; k < W; k += 2) {
+                const float2 q = *reinterpret_cast<const float2 *>(src + k);
+                w[k] = q.x;
+                w[k + 1] = q.y;
+            }
+            return;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) w[k] = src[k];
+}
+
+// BS x BS block from shared memory (16-byte load for a 2x2 FP32 block: records are 16-byte
+// aligned and 2x2 blocks lie on 16-byte boundaries).
+template <typename T, int BS>
+__device__ __forceinline__ void load_blk(const T *src, T (&M)[BS][BS]) {
+    if constexpr (sizeof(T) == 4 && BS == 2) {
+        const float4 q = *reinterpret_cast<const float4 *>(src);
+        M[0][0] = q.x; M[0][1] = q.y; M[1][0] = q.z; M[1][1] = q.w;
     } else {
 #pragma unroll
-        for (int k = 0; k < W; ++k) w[k] = src[k];
+        for (int p = 0; p < BS; ++p)
+#pragma unroll
+            for (int q = 0; q < BS; ++q) M[p][q] = src[p * BS + q];
+    }
+}
+
+// Windowed scan value of chunk c (see the header): forward, the value entering c from the
+// `reach` chunks before it, z <- F_k z + o_k for k = max(0, c - reach) .. c-1; backward, the
+// value after c from the chunks after it, z <- H_k z + o_k for k = min(tact-1, c + reach) ..
+// c+1.  maps: the line's F or H blocks; off: the line's chunk offsets (BS per chunk).
+template <typename T, int BS>
+__device__ __forceinline__ void win_scan(bool forward, int c, int tact, int reach, const T *maps, const T *off,
+                                         T (&z)[BS]) {
+#pragma unroll
+    for (int p = 0; p < BS; ++p) z[p] = T(0);
+    const int k0 = forward ? max(0, c - reach) : min(tact - 1, c + reach);
+    const int n = forward ? c - k0 : k0 - c;
+    for (int t = 0; t < n; ++t) {
+        const int k = forward ? k0 + t : k0 - t;
+        T M[BS][BS];
+        load_blk<T, BS>(maps + k * BS * BS, M);
+        T nz[BS];
+#pragma unroll
+        for (int p = 0; p < BS; ++p) {
+            T acc = off[k * BS + p];
+#pragma unroll
+            for (int q = 0; q < BS; ++q) acc += M[p][q] * z[q];
+            nz[p] = acc;
+        }
+#pragma unroll
+        for (int p = 0; p < BS; ++p) z[p] = nz[p];
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// One line group from its staged inputs.  nl lines of one simulation and direction, T
-// threads per line; thread (l, c) = (tid / T, tid % T) owns blocks [c M, c M + M) of line l.
+// One line group from its staged inputs: nl lines of one simulation and direction, Tl
+// threads per line; thread (l, c) = (tid / Tl, tid % Tl) owns middle blocks [c MM, c MM + MM).
 // ---------------------------------------------------------------------------------------
 template <typename T, int BS, int MM>
-__device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_raw, int natural,
-                                          Map<T, BS> *smmaps) {
+__device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_raw, int natural, int full_scan,
+                                          ScanSmem<T, BS> &ssm, T *offf, T *offb) {
+    static_assert(MM >= 2, "chunks of at least two blocks");
+    constexpr int W = BS == 2 ? 8 : 12;  // end windows (fac_win)
     constexpr int B2 = BS * BS;
-    const int tid = threadIdx.x;
-    const LineDesc<T> *descs = (const LineDesc<T> *)stage_raw;  // staged descriptors
+    const int tid = threadIdx.x, lane = tid & 31;
+    const LineDesc<T> *descs = (const LineDesc<T> *)stage_raw;
     const T *stage = (const T *)(stage_raw + fac_desc_area(gr.y));
-    const LineDesc<T> &d0 = descs[0];
-    const int N = d0.N;
-    const LineShape s = line_shape(d0.method, N);
-    const FGeom g = fgeom(s.nb, fac_mmax(d0.method));
-    const int Tl = g.T, M = g.M;
-    const int Lp = fac_lp(N), R = fac_rec(BS, Tl);
+    const FacGeom g = fac_geom(descs[0].method, descs[0].N);
+    const int N = g.N, Tl = g.T, tact = g.tact;
+    const int Lp = fac_lp(N), R = fac_rec(g);
     const int l = tid / Tl, c = tid % Tl;
-    const bool active = l < gr.y;
-    const LineDesc<T> &d = descs[active ? l : 0];
-    const T *sP = stage + (size_t)(active ? l : 0) * (3 * Lp + R);
+    const bool line_ok = l < gr.y;
+    const bool act = line_ok && c < tact;
+    const int ll = line_ok ? l : 0;
+    const LineDesc<T> &d = descs[ll];
+    const T *sP = stage + (size_t)ll * (3 * Lp + R);
     const T *sV = sP + Lp, *sA = sP + 2 * Lp, *sR = sP + 3 * Lp;
-    const T *eH = sR + fac_chunk_elems(BS, Tl), *eT = eH + kEndStride;  // end tables
-    const int pl = p_last(d0.method, N);
-    const int b0 = c * M;
-    int n = s.nb - b0;
-    n = n < 0 ? 0 : (n > M ? M : n);
-    if (!active) n = 0;
-    const bool has_first = active && c == 0;                   // owns block 0
-    const bool has_last = active && n > 0 && b0 + n == s.nb;  // owns block nb-1
+    const T *eH = sR + fac_chunk_elems(g), *eT = eH + fac_e_stride(g);
+    const int pl = p_last(g.method, N);
+    constexpr int Z = 2 * W + BS;
+    const T *sinfo = sR + fac_info(g);
+    T *lofff = offf + (tid - c) * BS, *loffb = offb + (tid - c) * BS;  // this line's chunk offsets
     const T ih = (T)d.inv_h, beta = (T)d.beta;
+    // segment of lanes that evaluates a line end: the whole warp for Tl >= 32, else the line
+    const int S = Tl < 32 ? Tl : 32;
+    const int ls = c % S;                 // lane index within the segment
+    const int sbase = lane - ls;          // first lane of the segment
+    const int wl = c >> 5;                // warp index within the line (Tl >= 32)
+    const bool head_seg = Tl < 32 || wl == 0;
+    const bool tail_seg = Tl < 32 || wl == ((tact - 1) >> 5);
+    const bool is_tail = act && c == tact - 1;
+    const int opT = pl + 1 - W, ovT = N + 1 - W;  // tail windows
 
-    // ---- alpha window and right-hand sides (from shared memory) ----
+    // ---- right-hand sides and the alpha window ----
     constexpr int NA = (BS == 2) ? MM + 2 : 3 * MM;
-    T aw[NA];     // CFD: 3 alpha / h at nodes b0+2 ..;  MFD: alpha at the chunk's cells
+    T aw[NA];     // CFD: 3 alpha / h at nodes jb-1 .. jb+MM;  MFD: alpha at the chunk's cells
     T Y[MM][BS];  // r, then y, then x
-    const int cb = s.hu + 1 + 3 * b0;  // MFD: first cell of the chunk
-    if constexpr (BS == 2) {
-        // windows s[b0 .. b0+MM+3] (the reads stay inside the stage buffer)
-        static_assert(MM % 4 == 0, "CFD window length");
-        const T c3 = T(3) * ih;
-        // node j = b0 + i + 3 is window index i + 3
-        {
-            T w[MM + 4];
+    const int jb = g.first + c * MM;      // CFD: first node of the chunk
+    const int cb = g.first + 3 * c * MM;  // MFD: first cell of the chunk
+    if (act) {
+        if constexpr (BS == 2) {
+            const T c3 = T(3) * ih;
+            T w[MM + 2];
+            load_win<T, MM + 2>(sA + jb - 1, w);
 #pragma unroll
-            for (int k = 0; k < MM + 4; ++k) w[k] = T(0);
-            if (n > 0) load_window<T, MM + 4>(sA + b0, w);
+            for (int k = 0; k < NA; ++k) aw[k] = c3 * w[k];
+            load_win<T, MM + 2>(sV + jb - 1, w);
 #pragma unroll
-            for (int k = 0; k < NA; ++k) aw[k] = (k < n + 2) ? c3 * w[k + 2] : T(0);
-        }
-        {
-            T w[MM + 4];
+            for (int i = 0; i < MM; ++i) Y[i][0] = c3 * (w[i + 2] - w[i]);
+            load_win<T, MM + 2>(sP + jb - 1, w);
 #pragma unroll
-            for (int k = 0; k < MM + 4; ++k) w[k] = T(0);
-            if (n > 0) load_window<T, MM + 4>(sV + b0, w);
+            for (int i = 0; i < MM; ++i) Y[i][1] = c3 * (w[i + 2] - w[i]);
+        } else {
 #pragma unroll
-            for (int i = 0; i < MM; ++i) Y[i][0] = (i < n) ? c3 * (w[i + 4] - w[i + 2]) : T(0);
-        }
-        {
-            T w[MM + 4];
+            for (int k = 0; k < NA; ++k) aw[k] = sA[cb + k];
+            T vw[3 * MM + 3];
 #pragma unroll
-            for (int k = 0; k < MM + 4; ++k) w[k] = T(0);
-            if (n > 0) load_window<T, MM + 4>(sP + b0, w);
-#pragma unroll
-            for (int i = 0; i < MM; ++i) Y[i][1] = (i < n) ? c3 * (w[i + 4] - w[i + 2]) : T(0);
-        }
-    } else {
-        const int na = 3 * n;
-#pragma unroll
-        for (int k = 0; k < NA; ++k) aw[k] = (k < na) ? sA[cb + k] : T(0);
-#pragma unroll
-        for (int i = 0; i < MM; ++i) {
-            if (i < n) {
-                {
-                    const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        const int cc = cb + 3 * i + m;
-                        const T dv = w0 * sV[cc - 2] + w1 * sV[cc - 1] + w2 * sV[cc] + w3 * sV[cc + 1];
-                        Y[i][m] = sP[cc] - aw[3 * i + m] * ih * dv;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int p = 0; p < BS; ++p) Y[i][p] = T(0);
-            }
-        }
-    }
-    // end windows z = [p window, v window, x of the adjacent block] (x filled later)
-    auto end_window = [&](bool tail, T (&z)[19]) {
-        const int op = tail ? pl - 7 : 0, ov = tail ? N - 7 : 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) { z[k] = sP[op + k]; z[8 + k] = sV[ov + k]; }
-#pragma unroll
-        for (int k = 16; k < 19; ++k) z[k] = T(0);
-    };
-    if (has_first) {  // head elimination: r_0 += KZ_head z
-        T z[19];
-        end_window(false, z);
-#pragma unroll
-        for (int p = 0; p < BS; ++p) {
-            T acc = T(0);
-#pragma unroll
-            for (int k = 0; k < 16; ++k) acc += eH[kEndKZ + p * 16 + k] * z[k];
-            Y[0][p] += acc;
-        }
-    }
-    if (has_last) {  // tail elimination: r_{nb-1} += KZ_tail z
-        T z[19];
-        end_window(true, z);
-        const int il = n - 1;
-#pragma unroll
-        for (int p = 0; p < BS; ++p) {
-            T acc = T(0);
-#pragma unroll
-            for (int k = 0; k < 16; ++k) acc += eT[kEndKZ + p * 16 + k] * z[k];
+            for (int k = 0; k < 3 * MM + 3; ++k) vw[k] = sV[cb - 2 + k];
+            const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
 #pragma unroll
             for (int i = 0; i < MM; ++i)
-                if (i == il) Y[i][p] += acc;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const int k = 3 * i + m;
+                    const T dv = w0 * vw[k] + w1 * vw[k + 1] + w2 * vw[k + 2] + w3 * vw[k + 3];
+                    Y[i][m] = sP[cb + k] - aw[k] * ih * dv;
+                }
         }
+    }
+
+    // ---- head / tail corrections of the adjacent blocks' right-hand sides (KZ z) ----
+    auto zval = [&](bool tail, int k) -> T {
+        return k < W ? sP[(tail ? opT : 0) + k] : sV[(tail ? ovT : 0) + k - W];
+    };
+    auto seg_kz = [&](bool tail, T (&out)[BS]) {
+        const T *kz = (tail ? eT : eH);
+#pragma unroll
+        for (int p = 0; p < BS; ++p) {
+            T acc = T(0);
+            for (int k = ls; k < 2 * W; k += S) acc += kz[p * 2 * W + k] * zval(tail, k);
+            out[p] = acc;
+        }
+        for (int o = S >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int p = 0; p < BS; ++p) out[p] += __shfl_xor_sync(0xffffffffu, out[p], o, S);
+    };
+    if (head_seg) {
+        T kz[BS];
+        seg_kz(false, kz);
+        if (act && c == 0)
+#pragma unroll
+            for (int p = 0; p < BS; ++p) Y[0][p] += kz[p];
+    }
+    if (tail_seg) {
+        T kz[BS];
+        seg_kz(true, kz);
+        if (is_tail)
+#pragma unroll
+            for (int p = 0; p < BS; ++p) Y[MM - 1][p] += kz[p];
     }
 
     // ---- block couplings from the alpha window ----
-    // A_i (to block i-1), B_i (diagonal, without the head/tail corrections), C_i (to i+1).
     auto blockA = [&](int i, T (&A)[BS][BS]) {
         if constexpr (BS == 2) {
             const T tb = T(3) * ih * beta;
@@ -662,6 +828,19 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
                 const T sc = aw[3 * i + m] * bh2;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) A[m][q] = (q >= m) ? -sc * (T)mim_DG(q - m) : T(0);
+            }
+        }
+    };
+    auto blockB = [&](int i, T (&B)[BS][BS]) {
+        if constexpr (BS == 2) {
+            B[0][0] = T(4); B[0][1] = T(0); B[1][0] = T(0); B[1][1] = T(4);
+        } else {
+            const T bh2 = beta * ih * ih;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const T sc = aw[3 * i + m] * bh2;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) B[m][q] = (q == m ? T(1) : T(0)) - sc * (T)mim_DG(q - m + 3);
             }
         }
     };
@@ -679,390 +858,285 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
             }
         }
     };
-    auto blockB = [&](int i, T (&B)[BS][BS]) {
-        if constexpr (BS == 2) {
-            B[0][0] = T(4); B[0][1] = T(0); B[1][0] = T(0); B[1][1] = T(4);
-        } else {
-            const T bh2 = beta * ih * ih;
+    // out = -Si (M v)
+    auto neg_si_mv = [&](const T (&Si)[BS][BS], const T (&M)[BS][BS], const T (&v)[BS], T (&out)[BS]) {
+        T t[BS];
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const T sc = aw[3 * i + m] * bh2;
+        for (int p = 0; p < BS; ++p) {
+            T acc = T(0);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) B[m][q] = (q == m ? T(1) : T(0)) - sc * (T)mim_DG(q - m + 3);
-            }
+            for (int q = 0; q < BS; ++q) acc += M[p][q] * v[q];
+            t[p] = acc;
+        }
+#pragma unroll
+        for (int p = 0; p < BS; ++p) {
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < BS; ++q) acc -= Si[p][q] * t[q];
+            out[p] = acc;
         }
     };
 
-    // ---- factorisation of the chunk and the local forward pass ----
+    // ---- factorisation and local forward pass ----
     T Si[MM][BS][BS];
-    T y[BS];
-#pragma unroll
-    for (int p = 0; p < BS; ++p) y[p] = T(0);
-    {
+    if (act) {
         T G[BS][BS];
 #pragma unroll
-        for (int p = 0; p < BS; ++p)
-#pragma unroll
-            for (int q = 0; q < BS; ++q) G[p][q] = T(0);
-#pragma unroll
         for (int i = 0; i < MM; ++i) {
-            if (i < n) {
-                T S[BS][BS];
-                if (i == 0) {
+            T S[BS][BS];
+            if (i == 0) {
+                load_blk<T, BS>(sR + c * B2, S);
+            } else {
+                T A[BS][BS], B[BS][BS];
+                blockA(i, A);
+                blockB(i, B);
+#pragma unroll
+                for (int p = 0; p < BS; ++p)
+#pragma unroll
+                    for (int q = 0; q < BS; ++q) {
+                        T acc = B[p][q];
+#pragma unroll
+                        for (int k = 0; k < BS; ++k) acc -= A[p][k] * G[k][q];
+                        S[p][q] = acc;
+                    }
+                if (i == MM - 1 && is_tail) {
 #pragma unroll
                     for (int p = 0; p < BS; ++p)
 #pragma unroll
-                        for (int q = 0; q < BS; ++q) S[p][q] = sR[c * B2 + p * BS + q];
-                } else {
-                    T A[BS][BS], B[BS][BS];
-                    blockA(i, A);
-                    blockB(i, B);
-#pragma unroll
-                    for (int p = 0; p < BS; ++p)
-#pragma unroll
-                        for (int q = 0; q < BS; ++q) {
-                            T acc = B[p][q];
-#pragma unroll
-                            for (int k = 0; k < BS; ++k) acc -= A[p][k] * G[k][q];
-                            S[p][q] = acc;
-                        }
-                    if (b0 + i == s.nb - 1) {
-#pragma unroll
-                        for (int p = 0; p < BS; ++p)
-#pragma unroll
-                            for (int q = 0; q < BS; ++q) S[p][q] -= eT[kEndDB + p * 3 + q];
-                    }
-                }
-                mat_inv<T, BS>(S, Si[i]);
-                // y <- S^{-1} (r - A y)   (y = 0 entering the chunk)
-                T t[BS];
-                if (i == 0) {
-#pragma unroll
-                    for (int p = 0; p < BS; ++p) t[p] = Y[i][p];
-                } else {
-                    T A[BS][BS];
-                    blockA(i, A);
-#pragma unroll
-                    for (int p = 0; p < BS; ++p) {
-                        T acc = Y[i][p];
-#pragma unroll
-                        for (int q = 0; q < BS; ++q) acc -= A[p][q] * y[q];
-                        t[p] = acc;
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < BS; ++p) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int q = 0; q < BS; ++q) acc += Si[i][p][q] * t[q];
-                    y[p] = acc;
-                    Y[i][p] = acc;
-                }
-                if (i + 1 < MM) {  // G <- S^{-1} C for the next block
-                    T C[BS][BS];
-                    blockC(i, C);
-                    f_mm<T, BS>(Si[i], C, G);
+                        for (int q = 0; q < BS; ++q) S[p][q] -= eT[fac_e_db(g) + p * BS + q];
                 }
             }
-        }
-    }
-
-    // ---- forward scan: the true y entering the chunk ----
-    Map<T, BS> mp;
-    {
-        const T *F = sR + Tl * B2 + c * B2;
+            mat_inv<T, BS>(S, Si[i]);
+            T t[BS];
+            if (i == 0) {
 #pragma unroll
-        for (int p = 0; p < BS; ++p) {
-            mp.off[p] = y[p];
-#pragma unroll
-            for (int q = 0; q < BS; ++q) mp.m[p][q] = active ? F[p * BS + q] : (p == q ? T(1) : T(0));
-        }
-    }
-    T yin[BS];
-    line_scan<T, BS>(mp, true, Tl, yin, smmaps);
-    {
-        // y_b += delta_b,  delta_b = -S_b^{-1} A_b delta_{b-1},  delta entering = yin
-        T dl[BS];
-#pragma unroll
-        for (int p = 0; p < BS; ++p) dl[p] = yin[p];
-#pragma unroll
-        for (int i = 0; i < MM; ++i) {
-            if (i < n) {
-                T A[BS][BS], t[BS];
+                for (int p = 0; p < BS; ++p) t[p] = Y[0][p];
+            } else {
+                T A[BS][BS];
                 blockA(i, A);
 #pragma unroll
                 for (int p = 0; p < BS; ++p) {
-                    T acc = T(0);
+                    T acc = Y[i][p];
 #pragma unroll
-                    for (int q = 0; q < BS; ++q) acc += A[p][q] * dl[q];
-                    t[p] = acc;
-                }
-#pragma unroll
-                for (int p = 0; p < BS; ++p) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int q = 0; q < BS; ++q) acc -= Si[i][p][q] * t[q];
-                    dl[p] = acc;
-                    Y[i][p] += acc;
-                }
-            }
-        }
-    }
-
-    // ---- local backward pass (x = 0 after the chunk) ----
-    T x[BS];
-#pragma unroll
-    for (int p = 0; p < BS; ++p) x[p] = T(0);
-#pragma unroll
-    for (int i = MM - 1; i >= 0; --i) {
-        if (i < n) {
-            T t[BS];
-            if (i == n - 1) {
-#pragma unroll
-                for (int p = 0; p < BS; ++p) t[p] = T(0);
-            } else {
-                T C[BS][BS];
-                blockC(i, C);
-#pragma unroll
-                for (int p = 0; p < BS; ++p) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int q = 0; q < BS; ++q) acc += C[p][q] * x[q];
+                    for (int q = 0; q < BS; ++q) acc -= A[p][q] * Y[i - 1][q];
                     t[p] = acc;
                 }
             }
 #pragma unroll
             for (int p = 0; p < BS; ++p) {
-                T acc = Y[i][p];
+                T acc = T(0);
 #pragma unroll
-                for (int q = 0; q < BS; ++q) acc -= Si[i][p][q] * t[q];
-                x[p] = acc;
+                for (int q = 0; q < BS; ++q) acc += Si[i][p][q] * t[q];
                 Y[i][p] = acc;
+            }
+            if (i + 1 < MM) {
+                T C[BS][BS];
+                blockC(i, C);
+                f_mm<T, BS>(Si[i], C, G);
             }
         }
     }
 
-    // ---- backward scan: the true x after the chunk ----
-    {
-        const T *H = sR + 2 * Tl * B2 + c * B2;
+    // ---- forward scan: the true y entering the chunk; correction ----
+    T yin[BS];
+    if (full_scan) {
+        Map<T, BS> mp;
+        if (act) {
+            load_blk<T, BS>(sR + tact * B2 + c * B2, mp.m);
 #pragma unroll
-        for (int p = 0; p < BS; ++p) {
-            mp.off[p] = x[p];
+            for (int p = 0; p < BS; ++p) mp.off[p] = Y[MM - 1][p];
+        } else {
+            map_id<T, BS>(mp);
+        }
+        seg_scan<T, BS>(mp, true, Tl, yin, ssm);
+    } else {
+        if (act)
 #pragma unroll
-            for (int q = 0; q < BS; ++q) mp.m[p][q] = active ? H[p * BS + q] : (p == q ? T(1) : T(0));
+            for (int p = 0; p < BS; ++p) lofff[c * BS + p] = Y[MM - 1][p];
+        __syncthreads();
+        if (act) win_scan<T, BS>(true, c, tact, (int)sinfo[0], sR + tact * B2, lofff, yin);
+    }
+    if (act) {
+        T dl[BS];
+#pragma unroll
+        for (int p = 0; p < BS; ++p) dl[p] = yin[p];
+#pragma unroll
+        for (int i = 0; i < MM; ++i) {
+            T A[BS][BS];
+            blockA(i, A);
+            neg_si_mv(Si[i], A, dl, dl);
+#pragma unroll
+            for (int p = 0; p < BS; ++p) Y[i][p] += dl[p];
+        }
+        // local backward pass (x = 0 after the chunk): x_i = y_i - Si_i (C_i x_{i+1})
+#pragma unroll
+        for (int i = MM - 2; i >= 0; --i) {
+            T C[BS][BS], t[BS];
+            blockC(i, C);
+            neg_si_mv(Si[i], C, Y[i + 1], t);
+#pragma unroll
+            for (int p = 0; p < BS; ++p) Y[i][p] += t[p];
         }
     }
+
+    // ---- backward scan: the true x after the chunk; correction ----
     T xin[BS];
-    line_scan<T, BS>(mp, false, Tl, xin, smmaps);
-    if (!active) return;
-    {
-        // x_b += eps_b,  eps_b = -S_b^{-1} C_b eps_{b+1},  eps after the chunk = xin
+    if (full_scan) {
+        Map<T, BS> mp;
+        if (act) {
+            load_blk<T, BS>(sR + 2 * tact * B2 + c * B2, mp.m);
+#pragma unroll
+            for (int p = 0; p < BS; ++p) mp.off[p] = Y[0][p];
+        } else {
+            map_id<T, BS>(mp);
+        }
+        seg_scan<T, BS>(mp, false, Tl, xin, ssm);
+    } else {
+        if (offb == offf) __syncthreads();  // one offset buffer: the forward reads are done
+        if (act)
+#pragma unroll
+            for (int p = 0; p < BS; ++p) loffb[c * BS + p] = Y[0][p];
+        __syncthreads();
+        if (act) win_scan<T, BS>(false, c, tact, (int)sinfo[1], sR + 2 * tact * B2, loffb, xin);
+    }
+    if (act) {
         T ep[BS];
 #pragma unroll
         for (int p = 0; p < BS; ++p) ep[p] = xin[p];
 #pragma unroll
         for (int i = MM - 1; i >= 0; --i) {
-            if (i < n) {
-                T t[BS];
-                if (b0 + i == s.nb - 1) {
+            T C[BS][BS];
+            blockC(i, C);
+            neg_si_mv(Si[i], C, ep, ep);
 #pragma unroll
-                    for (int p = 0; p < BS; ++p) t[p] = T(0);
-                } else {
-                    T C[BS][BS];
-                    blockC(i, C);
-#pragma unroll
-                    for (int p = 0; p < BS; ++p) {
-                        T acc = T(0);
-#pragma unroll
-                        for (int q = 0; q < BS; ++q) acc += C[p][q] * ep[q];
-                        t[p] = acc;
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < BS; ++p) {
-                    T acc = T(0);
-#pragma unroll
-                    for (int q = 0; q < BS; ++q) acc -= Si[i][p][q] * t[q];
-                    ep[p] = acc;
-                    Y[i][p] += acc;
-                }
-            }
+            for (int p = 0; p < BS; ++p) Y[i][p] += ep[p];
         }
     }
 
     // ---- outputs: C = 2 u* - a (+ source), v' = 2 v* - v, optionally natural u, w ----
-    bool hit = false;
-    const int src_k = d.src_k;
-    auto srcval = [&](int k) -> T {
-        if (k != src_k) return T(0);
-        hit = true;
-        const long long m = *d.clock;
-        return (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(m + 1) * d.dt));
-    };
-    T *__restrict__ uo = natural ? d.u_out : nullptr;
-    T *__restrict__ wo = natural ? d.w_out : nullptr;
-    const bool nat = uo != nullptr;
     T *__restrict__ gpo = d.po;
     T *__restrict__ gvo = d.vo;
-    const int spo = (int)d.spo, svo = (int)d.svo, snp = (int)d.snp, snv = (int)d.snv;
+    T *__restrict__ uo = natural ? d.u_out : nullptr;
+    T *__restrict__ wo = natural ? d.w_out : nullptr;
+    const long long spo = d.spo, svo = d.svo, snp = d.snp, snv = d.snv;
+    const int src_k = d.src_k;
+    // source term dt/2 f(t_{m+1}) added by the thread that wrote pressure point src_k
+    auto add_source = [&]() {
+        const long long m = *d.clock;
+        const T s = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(m + 1) * d.dt));
+        gpo[src_k * spo] = gpo[src_k * spo] + s;
+        if (d.advance_clock) *d.clock = m + 1;
+    };
     auto out_p = [&](int k, T val_out, T val_nat) {
-        gpo[k * spo] = val_out + srcval(k);
-        if (nat) uo[k * snp] = val_nat;
+        gpo[k * spo] = val_out;
+        if (uo) uo[k * snp] = val_nat;
     };
     auto out_v = [&](int j, T vin, T dv) {  // dv = beta * (D_u u*)_j
         gvo[j * svo] = vin - T(2) * dv;
-        if (nat) wo[j * snv] = vin - dv;
+        if (wo) wo[j * snv] = vin - dv;
     };
-    if constexpr (BS == 2) {
-        // node j = b0 + i + 3 is window index i + 3 (16-byte loads of the chunk's windows)
-        {
-            T wp[MM + 4], wa[MM + 4];
-            if (n > 0) {
-                load_window<T, MM + 4>(sP + b0, wp);
-                load_window<T, MM + 4>(sA + b0, wa);
+    if (act) {
+        if constexpr (BS == 2) {
+            T wp[MM + 2], wa[MM + 2], wv[MM + 2];
+            load_win<T, MM + 2>(sP + jb - 1, wp);
+            load_win<T, MM + 2>(sA + jb - 1, wa);
+            load_win<T, MM + 2>(sV + jb - 1, wv);
+#pragma unroll
+            for (int i = 0; i < MM; ++i) {
+                const T ae = wa[i + 1] * Y[i][0];
+                out_p(jb + i, wp[i + 1] - T(2) * ae, wp[i + 1] - ae);
+                out_v(jb + i, wv[i + 1], beta * Y[i][1]);
             }
+            if (src_k >= jb && src_k < jb + MM) add_source();
+        } else {
+            const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
+            const T bi = beta * ih;
 #pragma unroll
-            for (int i = 0; i < MM; ++i)
-                if (i < n) {
-                    const T pin = wp[i + 3];
-                    const T ae = wa[i + 3] * Y[i][0];
-                    out_p(b0 + i + 3, pin - T(2) * ae, pin - ae);
-                }
-        }
-        {
-            T wv[MM + 4];
-            if (n > 0) load_window<T, MM + 4>(sV + b0, wv);
-#pragma unroll
-            for (int i = 0; i < MM; ++i)
-                if (i < n) out_v(b0 + i + 3, wv[i + 3], beta * Y[i][1]);
-        }
-    } else {
-        T xn[BS];  // x of the block after the current one
-#pragma unroll
-        for (int p = 0; p < BS; ++p) xn[p] = xin[p];
-#pragma unroll
-        for (int i = MM - 1; i >= 0; --i) {
-            if (i < n) {
-                const int b = b0 + i;
+            for (int i = 0; i < MM; ++i) {
                 const int q0 = cb + 3 * i;
 #pragma unroll
                 for (int m = 0; m < 3; ++m) out_p(q0 + m, T(2) * Y[i][m] - sP[q0 + m], Y[i][m]);
-                if (b != s.nb - 1) {
-                    // nodes q0+1..q0+3 from this block's cells and the next block's
-                    const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
-                    const T bi = beta * ih;
-                    out_v(q0 + 1, sV[q0 + 1], bi * (w0 * Y[i][0] + w1 * Y[i][1] + w2 * Y[i][2] + w3 * xn[0]));
-                    out_v(q0 + 2, sV[q0 + 2], bi * (w0 * Y[i][1] + w1 * Y[i][2] + w2 * xn[0] + w3 * xn[1]));
-                    out_v(q0 + 3, sV[q0 + 3], bi * (w0 * Y[i][2] + w1 * xn[0] + w2 * xn[1] + w3 * xn[2]));
+                // x of the next block (the next chunk's first block after the last one)
+                const int in = i + 1 < MM ? i + 1 : i;
+                const T xn0 = i + 1 < MM ? Y[in][0] : xin[0];
+                const T xn1 = i + 1 < MM ? Y[in][1] : xin[1];
+                const T xn2 = i + 1 < MM ? Y[in][2] : xin[2];
+                if (!(i == MM - 1 && is_tail)) {
+                    out_v(q0 + 1, sV[q0 + 1], bi * (w0 * Y[i][0] + w1 * Y[i][1] + w2 * Y[i][2] + w3 * xn0));
+                    out_v(q0 + 2, sV[q0 + 2], bi * (w0 * Y[i][1] + w1 * Y[i][2] + w2 * xn0 + w3 * xn1));
+                    out_v(q0 + 3, sV[q0 + 3], bi * (w0 * Y[i][2] + w1 * xn0 + w2 * xn1 + w3 * xn2));
                 }
-#pragma unroll
-                for (int p = 0; p < BS; ++p) xn[p] = Y[i][p];
             }
+            if (src_k >= cb && src_k < cb + 3 * MM) add_source();
         }
     }
-    T xl[BS];  // x of the chunk's last block
+
+    // ---- head and tail regions, evaluated by their segments ----
+    auto seg_end = [&](bool tail) {
+        const T *et = tail ? eT : eH;
+        const int src_lane = sbase + ((tail ? tact - 1 : 0) % S);
+        T xJ[BS];
 #pragma unroll
-    for (int p = 0; p < BS; ++p) xl[p] = Y[0][p];
-#pragma unroll
-    for (int i = 1; i < MM; ++i)
-        if (i == n - 1)
-#pragma unroll
-            for (int p = 0; p < BS; ++p) xl[p] = Y[i][p];
-    if (has_last) {  // tail unknowns: xe = HZ z, z with the last block's x
-        T z[19], xe[6];
-        end_window(true, z);
-#pragma unroll
-        for (int p = 0; p < BS; ++p) z[16 + p] = xl[p];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
+        for (int b = 0; b < BS; ++b) xJ[b] = __shfl_sync(0xffffffffu, tail ? Y[MM - 1][b] : Y[0][b], src_lane);
+        if (!line_ok) return;
+        const int m = tail ? g.tu : g.hu;
+        auto row_dot = [&](const T *row) -> T {
             T acc = T(0);
+            for (int k = 0; k < 2 * W; ++k) acc += row[k] * zval(tail, k);
 #pragma unroll
-            for (int k = 0; k < 19; ++k) acc += eT[kEndHZ + q * 19 + k] * z[k];
-            xe[q] = acc;
-        }
+            for (int b = 0; b < BS; ++b) acc += row[2 * W + b] * xJ[b];
+            return acc;
+        };
         if constexpr (BS == 2) {
-            // e_{N-2}, g_{N-2}, e_{N-1}, g_{N-1}, g_N
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int j = N - 2 + q;
-                const T pin = sP[j];
-                const T ae = sA[j] * xe[2 * q];
-                out_p(j, pin - T(2) * ae, pin - ae);
-                out_v(j, sV[j], beta * xe[2 * q + 1]);
-            }
-            out_v(N, sV[N], beta * xe[4]);
-        } else {
-            // tail cells after this block, then nodes qb+1 .. N
-            const int qb = cb + 3 * (n - 1);
-            for (int t2 = 0; t2 < s.tu; ++t2) {
-                const int cc = qb + 3 + t2;
-                T xv = xe[0];
-#pragma unroll
-                for (int q = 1; q < 6; ++q)
-                    if (q == t2) xv = xe[q];
-                out_p(cc, T(2) * xv - sP[cc], xv);
-            }
-            for (int j = qb + 1; j <= N; ++j) {
-                const T *row = eT + kEndDZ + (j - qb - 1) * 19;
-                T acc = T(0);
-#pragma unroll
-                for (int k = 0; k < 19; ++k) acc += row[k] * z[k];
-                out_v(j, sV[j], beta * ih * acc);
-            }
-        }
-    }
-    if (has_first) {  // head unknowns from block 0: xe = HZ z, z with block 0's x
-        T z[19], xe[6];
-        end_window(false, z);
-#pragma unroll
-        for (int p = 0; p < BS; ++p) z[16 + p] = Y[0][p];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            T acc = T(0);
-#pragma unroll
-            for (int k = 0; k < 19; ++k) acc += eH[kEndHZ + q * 19 + k] * z[k];
-            xe[q] = acc;
-        }
-        if constexpr (BS == 2) {
-            // g0, e1, g1, e2, g2
-            out_v(0, sV[0], beta * xe[0]);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int j = 1 + q;
-                const T pin = sP[j];
-                const T ae = sA[j] * xe[1 + 2 * q];
-                out_p(j, pin - T(2) * ae, pin - ae);
-                out_v(j, sV[j], beta * xe[2 + 2 * q]);
+            const int r0 = tail ? 2 * N - g.tu : 0;
+            for (int q = ls; q < m; q += S) {
+                const T x = row_dot(et + fac_e_hz(g) + q * Z);
+                const int i = r0 + q;
+                const bool is_g = (i == 0) || (i == 2 * N - 1) || (i % 2 == 0);
+                const int node = i == 0 ? 0 : (i == 2 * N - 1 ? N : (i + 1) / 2);
+                if (is_g) {
+                    out_v(node, sV[node], beta * x);
+                } else {
+                    const T ae = sA[node] * x;
+                    out_p(node, sP[node] - T(2) * ae, sP[node] - ae);
+                    if (node == src_k) add_source();
+                }
             }
         } else {
-            // head cells 1 .. hu, then nodes 0 .. hu+1
-#pragma unroll
-            for (int t2 = 0; t2 < 6; ++t2)
-                if (t2 < s.hu) out_p(1 + t2, T(2) * xe[t2] - sP[1 + t2], xe[t2]);
-            for (int j = 0; j <= s.hu + 1; ++j) {
-                const T *row = eH + kEndDZ + j * 19;
-                T acc = T(0);
-#pragma unroll
-                for (int k = 0; k < 19; ++k) acc += row[k] * z[k];
-                out_v(j, sV[j], beta * ih * acc);
+            const int cell0 = tail ? N - g.tu + 1 : 1;
+            for (int q = ls; q < m; q += S) {
+                const T x = row_dot(et + fac_e_hz(g) + q * Z);
+                const int cc = cell0 + q;
+                out_p(cc, T(2) * x - sP[cc], x);
+                if (cc == src_k) add_source();
+            }
+            const int qb = g.first + 3 * (g.nb - 1);
+            const int jlo = tail ? qb + 1 : 0, nrow = tail ? N - qb : g.hu + 2;
+            for (int q = ls; q < nrow; q += S) {
+                const int j = jlo + q;
+                out_v(j, sV[j], beta * ih * row_dot(et + fac_e_dz(g) + q * Z));
             }
         }
-    }
-    if (hit && d.advance_clock) *d.clock = *d.clock + 1;
+    };
+    if (head_seg) seg_end(false);
+    if (tail_seg) seg_end(true);
 }
 
 // ---------------------------------------------------------------------------------------
 // The kernel: persistent CTAs walk the line groups g = blockIdx.x, blockIdx.x + gridDim.x,
-// ...; with STAGES = 2 thread 0 starts the copies of the next group before the current one
+// ...; with two stages thread 0 starts the copies of the next group before the current one
 // is solved.  A wait that runs out sets *fault and ends the CTA.
 // ---------------------------------------------------------------------------------------
-template <typename T, int BS, int MM, int STAGES>
+template <typename T, int BS, int MM>
 __global__ void __launch_bounds__(kFacThreads, 1)
-line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const int4 *__restrict__ groups,
-                           int ngroups, int natural, unsigned stage_bytes, int *fault) {
+line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const int4 *__restrict__ groups, int ngroups,
+                           int natural, unsigned stage_bytes, int stages, int full_scan, int *fault) {
     extern __shared__ __align__(128) unsigned char fac_smem[];
-    __shared__ Map<T, BS> smmaps[32];
+    __shared__ ScanSmem<T, BS> ssm;
     __shared__ __align__(8) unsigned long long bars[2];
+    // chunk offsets of the windowed scans: forward and backward buffers for FP32, one for FP64
+    constexpr int kBufs = sizeof(T) == 4 ? 2 : 1;
+    __shared__ T offs[kBufs][kFacThreads * BS];
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -1070,74 +1144,76 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const int4 *__
         mbar_fence_init();
     }
     __syncthreads();
-    if (STAGES == 2 && tid == 0 && (int)blockIdx.x < ngroups)
-        fac_issue<T>(descs, groups[blockIdx.x], fac_smem, &bars[0]);
+    const bool two = stages == 2;
+    if (two && tid == 0 && (int)blockIdx.x < ngroups) fac_issue<T>(descs, groups[blockIdx.x], fac_smem, &bars[0]);
     int it = 0;
     bool ok = true;
-    int g = blockIdx.x;
-    for (; g < ngroups; g += gridDim.x, ++it) {
-        const int st = STAGES == 2 ? (it & 1) : 0;
-        const unsigned par = STAGES == 2 ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1);
+    int gi = blockIdx.x;
+    for (; gi < ngroups; gi += gridDim.x, ++it) {
+        const int st = two ? (it & 1) : 0;
+        const unsigned par = two ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1);
         if (tid == 0) {
-            if (STAGES == 2) {
-                const int gn = g + (int)gridDim.x;
-                if (gn < ngroups)
-                    fac_issue<T>(descs, groups[gn], fac_smem + (size_t)(st ^ 1) * stage_bytes, &bars[st ^ 1]);
+            if (two) {
+                const int gn = gi + (int)gridDim.x;
+                if (gn < ngroups) fac_issue<T>(descs, groups[gn], fac_smem + (size_t)(st ^ 1) * stage_bytes, &bars[st ^ 1]);
             } else {
-                fac_issue<T>(descs, groups[g], fac_smem, &bars[0]);
+                fac_issue<T>(descs, groups[gi], fac_smem, &bars[0]);
             }
         }
         const bool got = mbar_wait(&bars[st], par);
         if (!__syncthreads_and(got)) { ok = false; break; }
-        fac_group<T, BS, MM>(groups[g], fac_smem + (size_t)st * stage_bytes, natural, smmaps);
+        fac_group<T, BS, MM>(groups[gi], fac_smem + (size_t)st * stage_bytes, natural, full_scan, ssm, offs[0],
+                             offs[kBufs - 1]);
         __syncthreads();
     }
     if (!ok && tid == 0) {
         atomicExch(fault, 1);
         // let copies still in flight land before the CTA's shared memory is released
-        const int st = STAGES == 2 ? (it & 1) : 0;
-        (void)mbar_wait(&bars[st], STAGES == 2 ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1));
-        if (STAGES == 2 && g + (int)gridDim.x < ngroups)
-            (void)mbar_wait(&bars[st ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+        const int st = two ? (it & 1) : 0;
+        (void)mbar_wait(&bars[st], two ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1));
+        if (two && gi + (int)gridDim.x < ngroups) (void)mbar_wait(&bars[st ^ 1], (unsigned)(((it + 1) >> 1) & 1));
     }
 }
 
 template <typename T>
-cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, cudaStream_t s) {
+cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, double *ws, int *status, cudaStream_t s) {
     if (nlines <= 0) return cudaSuccess;
-    fac_precompute_kernel<T><<<(nlines + 63) / 64, 64, 0, s>>>(d, nlines);
+    fac_precompute_kernel<T><<<(nlines + 63) / 64, 64, 0, s>>>(d, nlines, ws, status);
     return cudaGetLastError();
 }
 
-template <typename T, int BS, int MM, int STAGES>
-cudaError_t launch_fac_inst(const LineDesc<T> *d, const int4 *groups, int ngroups, size_t stage_bytes,
-                            int grid, int natural, int *fault, cudaStream_t s) {
-    auto kern = line_solve_factored_kernel<T, BS, MM, STAGES>;
-    const size_t dyn = (size_t)STAGES * stage_bytes;
+template <typename T, int BS, int MM>
+cudaError_t launch_fac_inst(const LineDesc<T> *d, const int4 *groups, int ngroups, size_t stage_bytes, int stages,
+                            int grid, int natural, int full_scan, int *fault, cudaStream_t s) {
+    auto kern = line_solve_factored_kernel<T, BS, MM>;
+    const size_t dyn = (size_t)stages * stage_bytes;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kFacThreads, dyn, s>>>(d, groups, ngroups, natural, (unsigned)stage_bytes, fault);
+    kern<<<grid, kFacThreads, dyn, s>>>(d, groups, ngroups, natural, (unsigned)stage_bytes, stages, full_scan, fault);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups, int ngroups, int method,
-                                       size_t stage_bytes, int stages, int grid, int natural, int *fault,
-                                       cudaStream_t s) {
+cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups, int ngroups, int variant,
+                                       size_t stage_bytes, int stages, int grid, int natural, int max_reach,
+                                       int *fault, cudaStream_t s) {
     if (ngroups <= 0) return cudaSuccess;
     if (grid > ngroups) grid = ngroups;
-    if (method == kCFD)
-        return stages == 2 ? launch_fac_inst<T, 2, 8, 2>(d, groups, ngroups, stage_bytes, grid, natural, fault, s)
-                           : launch_fac_inst<T, 2, 8, 1>(d, groups, ngroups, stage_bytes, grid, natural, fault, s);
-    return stages == 2 ? launch_fac_inst<T, 3, 3, 2>(d, groups, ngroups, stage_bytes, grid, natural, fault, s)
-                       : launch_fac_inst<T, 3, 3, 1>(d, groups, ngroups, stage_bytes, grid, natural, fault, s);
+    if (stages != 1 && stages != 2) return cudaErrorInvalidValue;
+    const int full = max_reach > kFacMaxReach ? 1 : 0;
+    switch (variant) {
+    case 0: return launch_fac_inst<T, 2, 9>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 1: return launch_fac_inst<T, 3, 2>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 2: return launch_fac_inst<T, 3, 3>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_fac_precompute<float>(const LineDesc<float> *, int, cudaStream_t);
-template cudaError_t launch_fac_precompute<double>(const LineDesc<double> *, int, cudaStream_t);
-template cudaError_t launch_line_solve_factored<float>(const LineDesc<float> *, const int4 *, int, int, size_t,
+template cudaError_t launch_fac_precompute<float>(const LineDesc<float> *, int, double *, int *, cudaStream_t);
+template cudaError_t launch_fac_precompute<double>(const LineDesc<double> *, int, double *, int *, cudaStream_t);
+template cudaError_t launch_line_solve_factored<float>(const LineDesc<float> *, const int4 *, int, int, size_t, int,
                                                        int, int, int, int *, cudaStream_t);
-template cudaError_t launch_line_solve_factored<double>(const LineDesc<double> *, const int4 *, int, int,
-                                                        size_t, int, int, int, int *, cudaStream_t);
+template cudaError_t launch_line_solve_factored<double>(const LineDesc<double> *, const int4 *, int, int, size_t,
+                                                        int, int, int, int, int *, cudaStream_t);
 
 }  // namespace adi

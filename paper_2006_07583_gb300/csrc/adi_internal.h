@@ -62,18 +62,25 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
 size_t v1_scratch_words(int method, int N);
 
 // Factored solver (adi_factored.cu).
-bool fac_supported(int method, int N, size_t esz);  // chunk fits registers, stage fits smem
-size_t fac_words(int method, int N);     // elements of one line's chunk record
-int fac_chunks(int method, int N);       // chunks (threads) per line, a power of two
+bool fac_supported(int method, int N, size_t esz);  // chunks fit a CTA, stage fits smem
+size_t fac_words(int method, int N);     // elements of one line's record
+int fac_chunks(int method, int N);       // threads per line
+int fac_variant(int method, int N);      // compiled kernel instance: 0 CFD, 1-2 MFD
+constexpr int kFacVariants = 3;
 int fac_lines_per_cta(int method, int N, size_t esz);
 size_t fac_stage_bytes(int method, int N, int nl, size_t esz);  // shared memory of one stage
-int fac_stages_for(size_t stage_bytes);  // 2 (prefetch), 1, or 0 (does not fit)
+int fac_stages_for(size_t stage_bytes, size_t esz);  // 2 (prefetch), 1, or 0 (does not fit)
+size_t fac_ws_doubles();                 // FP64 workspace per line of the precompute
+// status[0]: set when a line system is singular; status[1]: atomic max of the lines' scan reach
 template <typename T>
-cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, cudaStream_t s);
+cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, double *ws, int *status,
+                                  cudaStream_t s);
+// max_reach: the largest scan reach of the launch's lines (beyond the window limit the
+// kernel uses the full scan)
 template <typename T>
 cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups, int ngroups,
-                                       int method, size_t stage_bytes, int stages, int grid,
-                                       int natural, int *fault, cudaStream_t s);
+                                       int variant, size_t stage_bytes, int stages, int grid,
+                                       int natural, int max_reach, int *fault, cudaStream_t s);
 
 // Chunked solver (adi_chunked.cu).
 int chunk_M(int method);                 // chunk length in blocks used by the kernel

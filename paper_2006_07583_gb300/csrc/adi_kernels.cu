@@ -22,85 +22,6 @@
 
 namespace adi {
 
-// ---------------------------------------------------------------------------------------
-// Full line system in solver ordering, FP64, for the boundary elimination.
-//   CFD ordering: g_0, e_1, g_1, ..., e_{N-1}, g_{N-1}, g_N  (e_j at 2j-1, g_j at 2j)
-//   MFD ordering: u_1 .. u_N (cell c at c-1)
-// ---------------------------------------------------------------------------------------
-template <typename T>
-__device__ double line_entry(const LineDesc<T> &d, int row, int col) {
-    const int N = d.N;
-    const double ih = d.inv_h, beta = d.beta;
-    double w[8];
-    int c0, n;
-    double acc = 0.0;
-    if (d.method == kCFD) {
-        bool is_g = (row == 0) || (row == 2 * N - 1) || (row % 2 == 0);
-        int node = row == 0 ? 0 : (row == 2 * N - 1 ? N : (row + 1) / 2);
-        if (is_g) {
-            n = cfd_P_row(N, node, &c0, w);
-            for (int t = 0; t < n; ++t)
-                if (cfd_idx_g(N, c0 + t) == col) acc += w[t];
-            n = cfd_Q_row(N, node, &c0, w);
-            for (int t = 0; t < n; ++t) {
-                int k = c0 + t;
-                if (k >= 1 && k <= N - 1 && cfd_idx_e(k) == col)
-                    acc += w[t] * ih * (double)d.alpha[k * d.sp];
-            }
-        } else {
-            n = cfd_Pbar_row(N, node, &c0, w);
-            for (int t = 0; t < n; ++t)
-                if (cfd_idx_e(c0 + t) == col) acc += w[t];
-            n = cfd_Qbar_row(N, node, &c0, w);
-            for (int t = 0; t < n; ++t)
-                if (cfd_idx_g(N, c0 + t) == col) acc += w[t] * ih * beta;
-        }
-        return acc;
-    }
-    // MFD Schur row for cell c = row + 1, column cell c' = col + 1.
-    const int c = row + 1, cc = col + 1;
-    double dw[8], gw[8];
-    int d0, g0;
-    int nd = mfd_D_row(N, c - 1, &d0, dw);
-    double s = 0.0;
-    for (int t = 0; t < nd; ++t) {
-        int node = d0 + t;
-        int ng = mfd_G_row(N, node, &g0, gw);
-        int k = cc - g0;
-        if (k >= 0 && k < ng) s += dw[t] * gw[k];
-    }
-    acc = (row == col ? 1.0 : 0.0) - (double)d.alpha[c * d.sp] * beta * ih * ih * s;
-    return acc;
-}
-
-// In-place Gauss-Jordan inverse with partial pivoting of an n x n (n <= 6) matrix.
-__device__ bool small_inverse(double *A, int n, double *R) {
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) R[i * n + j] = (i == j) ? 1.0 : 0.0;
-    double scale = 0.0;
-    for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(A[i]));
-    for (int c = 0; c < n; ++c) {
-        int p = c;
-        for (int i = c + 1; i < n; ++i)
-            if (fabs(A[i * n + c]) > fabs(A[p * n + c])) p = i;
-        if (!(fabs(A[p * n + c]) > 1e-13 * scale)) return false;
-        if (p != c)
-            for (int j = 0; j < n; ++j) {
-                double t = A[c * n + j]; A[c * n + j] = A[p * n + j]; A[p * n + j] = t;
-                t = R[c * n + j]; R[c * n + j] = R[p * n + j]; R[p * n + j] = t;
-            }
-        double ip = 1.0 / A[c * n + c];
-        for (int j = 0; j < n; ++j) { A[c * n + j] *= ip; R[c * n + j] *= ip; }
-        for (int i = 0; i < n; ++i) {
-            if (i == c) continue;
-            double f = A[i * n + c];
-            if (f == 0.0) continue;
-            for (int j = 0; j < n; ++j) { A[i * n + j] -= f * A[c * n + j]; R[i * n + j] -= f * R[c * n + j]; }
-        }
-    }
-    return true;
-}
-
 // One thread per line: head and tail elimination tables.
 template <typename T>
 __global__ void precompute_kernel(const LineDesc<T> *__restrict__ descs, int nlines,

@@ -209,10 +209,12 @@ def test_nonfinite_detected(adi):
 
 
 # multi-chunk lines.  Chunked solver: chunks of <= 32 (CFD) / 16 (MFD) blocks with separators.
-# Factored solver: a power-of-two number of chunks per line of <= 8 (CFD) / 3 (MFD) blocks;
-# these sizes give ragged and empty trailing chunks and lines spanning 1, 2 and more warps.
+# Factored solver: chunks of exactly 8 (CFD) / 2 or 3 (MFD) blocks, the remainder absorbed by
+# the line ends; these sizes give every remainder, idle trailing threads, lines spanning 1, 2
+# and more warps, and the longest lines of the bench (4096 cells: 512 and 480 threads per line,
+# the three-block MFD chunks).
 MULTI = [(CFD, 230, 171), (MFD, 260, 197), (CFD, 97, 400), (MFD, 53, 311), (CFD, 400, 150),
-         (MFD, 500, 97)]
+         (MFD, 500, 97), (CFD, 4096, 19), (MFD, 4096, 17), (MFD, 3500, 24)]
 
 
 @pytest.mark.parametrize("solver", [1, 2])
