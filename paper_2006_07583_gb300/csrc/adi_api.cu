@@ -416,7 +416,8 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
     p.precision = prec;
     const size_t dsz = desc_size(prec), esz = elem_size(prec);
     std::vector<unsigned char> v1[2][2], cd[2][2], fdv[2][2];
-    std::vector<int4> gr[2][2], fgr[2][kFacVariants];
+    std::vector<int4> gr[2][2];
+    std::vector<FacGroup> fgr[2][kFacVariants];
     size_t words = 0;
     for (adi_sim *s : members) {
         for (int dir = 0; dir < 2; ++dir) {
@@ -433,7 +434,7 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                 int v = fac_variant(s->g.method, N);
                 for (int st = 0; st < n; st += nl) {
                     int cnt = std::min(nl, n - st);
-                    fgr[dir][v].push_back(make_int4(first + st, cnt, s->g.method, 0));
+                    fgr[dir][v].push_back(fac_group_of(s->g.method, N, first + st, cnt, 1.0 / s->h, 0.5 * s->dt));
                     p.fstage[dir][v] = std::max(p.fstage[dir][v], fac_stage_bytes(s->g.method, N, cnt, esz));
                 }
                 p.freach[dir][v] = std::max(p.freach[dir][v], s->fac_reach);
@@ -490,8 +491,8 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
             p.fgrid[dir][v] = std::min(p.nfgroups[dir][v], sm_count());
             if (p.nfgroups[dir][v] && !p.fstages[dir][v]) { rc = ADI_ENOTSUP; break; }
             if (!fgr[dir][v].empty()) {
-                rc = dev_alloc(p.fgroups[dir][v], fgr[dir][v].size() * sizeof(int4));
-                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fgroups[dir][v].p, fgr[dir][v].data(), fgr[dir][v].size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+                rc = dev_alloc(p.fgroups[dir][v], fgr[dir][v].size() * sizeof(FacGroup));
+                if (!rc) rc = cuda_status(cudaMemcpyAsync(p.fgroups[dir][v].p, fgr[dir][v].data(), fgr[dir][v].size() * sizeof(FacGroup), cudaMemcpyHostToDevice, stream));
             }
         }
         for (int m = 0; m < 2 && !rc; ++m) {
@@ -525,7 +526,7 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
     for (int v = 0; v < kFacVariants && e == cudaSuccess; ++v)
         if (p.nfgroups[dir][v])
             e = launch_line_solve_factored<T>((const LineDesc<T> *)p.fd[q][dir].p,
-                                              (const int4 *)p.fgroups[dir][v].p, p.nfgroups[dir][v], v,
+                                              (const FacGroup *)p.fgroups[dir][v].p, p.nfgroups[dir][v], v,
                                               p.fstage[dir][v], p.fstages[dir][v], p.fgrid[dir][v], nat,
                                               p.freach[dir][v], (int *)p.fault.p, stream);
     for (int m = 0; m < 2 && e == cudaSuccess; ++m)

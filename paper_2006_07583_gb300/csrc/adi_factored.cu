@@ -40,8 +40,9 @@
 
 namespace adi {
 
-constexpr int kFacThreads = 512;              // threads per CTA
-constexpr int kFacMaxT = 512;                 // chunks (threads) per line at most
+constexpr int kFacThreads = 512;              // threads per CTA: 15 compute warps and one staging warp
+constexpr int kFacWorkers = kFacThreads - 32; // threads that solve lines
+constexpr int kFacMaxT = kFacWorkers;         // chunks (threads) per line at most
 constexpr size_t kFacSmemLimit = 227 * 1024;  // shared memory per CTA
 constexpr size_t kFacStaticBase = 4096;       // reserve for the kernel's other static shared memory
 constexpr int kFacWs = 1024;                  // FP64 workspace of the precompute, per line
@@ -117,15 +118,25 @@ __host__ __device__ inline int fac_info(const FacGeom &g) { return fac_chunk_ele
 __host__ __device__ inline int fac_rec(const FacGeom &g) { return fac_info(g) + 4; }
 // Elements of one staged line array (pressure, velocity or alpha), a multiple of four.
 __host__ __device__ inline int fac_lp(int N) { return (N + 2 + 3) & ~3; }
-__host__ __device__ inline int fac_line_elems(const FacGeom &g) { return 3 * fac_lp(g.N) + fac_rec(g); }
+// Shared-memory scratch of a staged line: the window parts of its end-region rows.
+__host__ __device__ inline int fac_end_rows(int method) {
+    return 2 * (fac_hmax(method) + (method == kMFD ? fac_hmax(method) + 2 : 0));
+}
+__host__ __device__ inline int fac_scratch(const FacGeom &g) { return (fac_end_rows(g.method) + 3) & ~3; }
+// A staged line: pressure, velocity, alpha (fac_lp each), the record, the scratch.
+__host__ __device__ inline int fac_line_elems(const FacGeom &g) { return 3 * fac_lp(g.N) + fac_rec(g) + fac_scratch(g); }
 
 constexpr size_t kDescBytes = sizeof(LineDesc<float>);
 static_assert(sizeof(LineDesc<float>) == sizeof(LineDesc<double>), "descriptor sizes differ");
 static_assert(kDescBytes % 16 == 0, "descriptor size");
 __host__ __device__ inline size_t fac_desc_area(int nl) { return ((size_t)nl * kDescBytes + 127) & ~(size_t)127; }
+// A stage: the group (128 bytes), the descriptors, then the lines.
+constexpr size_t kFacGroupBytes = 128;
+static_assert(sizeof(FacGroup) % 16 == 0 && sizeof(FacGroup) <= kFacGroupBytes, "group header");
+__host__ __device__ inline size_t fac_head_bytes(int nl) { return kFacGroupBytes + fac_desc_area(nl); }
 
 size_t fac_stage_bytes(int method, int N, int nl, size_t esz) {
-    size_t b = fac_desc_area(nl) + (size_t)nl * fac_line_elems(fac_geom(method, N)) * esz;
+    size_t b = fac_head_bytes(nl) + (size_t)nl * fac_line_elems(fac_geom(method, N)) * esz;
     return (b + 127) & ~(size_t)127;
 }
 int fac_stages_for(size_t stage_bytes, size_t esz) {
@@ -137,7 +148,7 @@ int fac_stages_for(size_t stage_bytes, size_t esz) {
 // would not fit shared memory.
 int fac_lines_per_cta(int method, int N, size_t esz) {
     const int T = fac_geom(method, N).T;
-    int nl = T >= kFacThreads ? 1 : kFacThreads / T;
+    int nl = T >= kFacWorkers ? 1 : kFacWorkers / T;
     while (nl > 1 && fac_stages_for(fac_stage_bytes(method, N, nl, esz), esz) < 2) --nl;
     return nl;
 }
@@ -151,6 +162,24 @@ size_t fac_words(int method, int N) { return (size_t)fac_rec(fac_geom(method, N)
 int fac_chunks(int method, int N) { return fac_geom(method, N).T; }
 int fac_variant(int method, int N) { return fac_variant_of(method, N); }
 size_t fac_ws_doubles() { return kFacWs; }
+FacGroup fac_group_of(int method, int N, int first, int nl, double inv_h, double beta) {
+    const FacGeom g = fac_geom(method, N);
+    FacGroup r;
+    r.first = first; r.nl = nl; r.N = N; r.T = g.T;
+    r.tact = g.tact; r.hu = g.hu; r.tu = g.tu; r.mid = g.first;
+    r.lp = fac_lp(N); r.rec = fac_rec(g);
+    r.eh = fac_chunk_elems(g); r.et = r.eh + fac_e_stride(g);
+    r.info = fac_info(g); r.pl = p_last(method, N);
+    r.ls = fac_line_elems(g); r.scr = 3 * r.lp + r.rec;
+    r.ih = inv_h; r.beta = beta; r.ihf = (float)inv_h; r.betaf = (float)beta; r.pad0 = r.pad1 = 0.f;
+    return r;
+}
+// Table offsets of an end region, as compile-time functions of the block size (fac_e_*).
+template <int BS>
+struct FacEnd {
+    static constexpr int W = BS == 2 ? 8 : 12, HMAX = BS == 2 ? 13 : 8, Z = 2 * W + BS;
+    static constexpr int HZ = BS * 2 * W, DZ = HZ + HMAX * Z, DB = DZ + (BS == 3 ? (HMAX + 2) * Z : 0);
+};
 
 // ---------------------------------------------------------------------------------------
 // Middle block b (A to block b-1, B, C to block b+1) in precision R from alpha values
@@ -507,6 +536,11 @@ __device__ __forceinline__ void map_shfl(Map<T, BS> &dst, const Map<T, BS> &src,
     }
 }
 
+// Barrier of the compute warps (named barrier 1; the staging warp does not take part).
+__device__ __forceinline__ void workers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kFacWorkers) : "memory");
+}
+
 // Scan buffers of a CTA: warp aggregates and warp prefixes.
 template <typename T, int BS>
 struct ScanSmem {
@@ -542,9 +576,9 @@ __device__ __forceinline__ void seg_scan(Map<T, BS> a, bool forward, int Tl, T (
     }
     const int nw = Tl >> 5;          // warps per line
     const int wl = warp % nw;        // warp index within its line
-    const bool whole = (tid / Tl) < (int)(blockDim.x / Tl);  // inside a whole line of the CTA
+    const bool whole = (tid / Tl) < (kFacWorkers / Tl);  // inside a whole line of the CTA
     if (pos == 31) sm.agg[warp] = a;  // the warp's full composition
-    __syncthreads();
+    workers_sync();
     if (whole && wl == 0 && lane == 0) {
         T p[BS];
 #pragma unroll
@@ -566,13 +600,44 @@ __device__ __forceinline__ void seg_scan(Map<T, BS> a, bool forward, int Tl, T (
             for (int i = 0; i < BS; ++i) p[i] = q[i];
         }
     }
-    __syncthreads();
+    workers_sync();
 #pragma unroll
     for (int i = 0; i < BS; ++i) {
         T acc = ex.off[i];
 #pragma unroll
         for (int k = 0; k < BS; ++k) acc += ex.m[i][k] * sm.pre[warp][k];
         z[i] = acc;
+    }
+}
+
+// Block inverse of the line kernel: the FP32 path takes the hardware reciprocal
+// approximation (relative error below 2^-22), FP64 an IEEE division.
+__device__ __forceinline__ float fac_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double fac_rcp(double x) { return 1.0 / x; }
+template <typename T, int BS>
+__device__ __forceinline__ void fac_inv(const T (&S)[BS][BS], T (&R)[BS][BS]) {
+    if constexpr (BS == 2) {
+        const T id = fac_rcp(S[0][0] * S[1][1] - S[0][1] * S[1][0]);
+        R[0][0] = S[1][1] * id; R[0][1] = -S[0][1] * id;
+        R[1][0] = -S[1][0] * id; R[1][1] = S[0][0] * id;
+    } else {
+        const T c00 = S[1][1] * S[2][2] - S[1][2] * S[2][1];
+        const T c01 = S[1][2] * S[2][0] - S[1][0] * S[2][2];
+        const T c02 = S[1][0] * S[2][1] - S[1][1] * S[2][0];
+        const T id = fac_rcp(S[0][0] * c00 + S[0][1] * c01 + S[0][2] * c02);
+        R[0][0] = c00 * id;
+        R[0][1] = (S[0][2] * S[2][1] - S[0][1] * S[2][2]) * id;
+        R[0][2] = (S[0][1] * S[1][2] - S[0][2] * S[1][1]) * id;
+        R[1][0] = c01 * id;
+        R[1][1] = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) * id;
+        R[1][2] = (S[0][2] * S[1][0] - S[0][0] * S[1][2]) * id;
+        R[2][0] = c02 * id;
+        R[2][1] = (S[0][1] * S[2][0] - S[0][0] * S[2][1]) * id;
+        R[2][2] = (S[0][0] * S[1][1] - S[0][1] * S[1][0]) * id;
     }
 }
 
@@ -625,21 +690,22 @@ __host__ __device__ inline unsigned round16(unsigned b) { return (b + 15u) & ~15
 // (padded leading dimensions) and the copies, rounded up to 16 bytes, stay inside the padded
 // line.
 template <typename T>
-__device__ void fac_issue(const LineDesc<T> *__restrict__ descs, int4 gr, unsigned char *stage,
+__device__ void fac_issue(const LineDesc<T> *__restrict__ descs, const FacGroup *gp, unsigned char *stage,
                           unsigned long long *bar) {
-    const LineDesc<T> &d0 = descs[gr.x];
-    const FacGeom g = fac_geom(d0.method, d0.N);
-    const int Lp = fac_lp(g.N), R = fac_rec(g);
-    const unsigned bp = round16((unsigned)(p_last(g.method, g.N) + 1) * (unsigned)sizeof(T));
-    const unsigned bv = round16((unsigned)(g.N + 1) * (unsigned)sizeof(T));
+    const FacGroup &gr = *gp;
+    const int Lp = gr.lp, R = gr.rec;
+    const unsigned bp = round16((unsigned)(gr.pl + 1) * (unsigned)sizeof(T));
+    const unsigned bv = round16((unsigned)(gr.N + 1) * (unsigned)sizeof(T));
     const unsigned br = (unsigned)R * (unsigned)sizeof(T);
-    const unsigned bd = (unsigned)(gr.y * kDescBytes);
-    mbar_expect_tx(bar, bd + (unsigned)gr.y * (2 * bp + bv + br));
-    bulk_to_smem(stage, descs + gr.x, bd, bar);
-    T *base = (T *)(stage + fac_desc_area(gr.y));
-    for (int l = 0; l < gr.y; ++l) {
-        const LineDesc<T> &d = descs[gr.x + l];
-        T *ln = base + (size_t)l * (3 * Lp + R);
+    const unsigned bd = (unsigned)(gr.nl * kDescBytes);
+    const unsigned bg = (unsigned)sizeof(FacGroup);
+    mbar_expect_tx(bar, bg + bd + (unsigned)gr.nl * (2 * bp + bv + br));
+    bulk_to_smem(stage, gp, bg, bar);
+    bulk_to_smem(stage + kFacGroupBytes, descs + gr.first, bd, bar);
+    T *base = (T *)(stage + fac_head_bytes(gr.nl));
+    for (int l = 0; l < gr.nl; ++l) {
+        const LineDesc<T> &d = descs[gr.first + l];
+        T *ln = base + (size_t)l * gr.ls;
         bulk_to_smem(ln, d.p, bp, bar);
         bulk_to_smem(ln + Lp, d.v, bv, bar);
         bulk_to_smem(ln + 2 * Lp, d.alpha, bp, bar);
@@ -714,30 +780,32 @@ __device__ __forceinline__ void win_scan(bool forward, int c, int tact, int reac
 // threads per line; thread (l, c) = (tid / Tl, tid % Tl) owns middle blocks [c MM, c MM + MM).
 // ---------------------------------------------------------------------------------------
 template <typename T, int BS, int MM>
-__device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_raw, int natural, int full_scan,
-                                          ScanSmem<T, BS> &ssm, T *offf, T *offb) {
+__device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural, int full_scan, ScanSmem<T, BS> &ssm,
+                                          T *offf, T *offb) {
     static_assert(MM >= 2, "chunks of at least two blocks");
-    constexpr int W = BS == 2 ? 8 : 12;  // end windows (fac_win)
+    using E = FacEnd<BS>;
+    constexpr int W = E::W;
     constexpr int B2 = BS * BS;
     const int tid = threadIdx.x, lane = tid & 31;
-    const LineDesc<T> *descs = (const LineDesc<T> *)stage_raw;
-    const T *stage = (const T *)(stage_raw + fac_desc_area(gr.y));
-    const FacGeom g = fac_geom(descs[0].method, descs[0].N);
-    const int N = g.N, Tl = g.T, tact = g.tact;
-    const int Lp = fac_lp(N), R = fac_rec(g);
-    const int l = tid / Tl, c = tid % Tl;
-    const bool line_ok = l < gr.y;
+    const FacGroup &gr = *(const FacGroup *)stage_raw;  // staged with the lines
+    const LineDesc<T> *descs = (const LineDesc<T> *)(stage_raw + kFacGroupBytes);
+    T *stage = (T *)(stage_raw + fac_head_bytes(gr.nl));
+    const int N = gr.N, Tl = gr.T, tact = gr.tact;
+    const int Lp = gr.lp, R = gr.rec;
+    const int l = tid / Tl, c = tid - l * Tl;
+    const bool line_ok = l < gr.nl;
     const bool act = line_ok && c < tact;
     const int ll = line_ok ? l : 0;
     const LineDesc<T> &d = descs[ll];
-    const T *sP = stage + (size_t)ll * (3 * Lp + R);
+    T *sPw = stage + (size_t)ll * gr.ls;
+    const T *sP = sPw;
     const T *sV = sP + Lp, *sA = sP + 2 * Lp, *sR = sP + 3 * Lp;
-    const T *eH = sR + fac_chunk_elems(g), *eT = eH + fac_e_stride(g);
-    const int pl = p_last(g.method, N);
-    constexpr int Z = 2 * W + BS;
-    const T *sinfo = sR + fac_info(g);
+    const T *eH = sR + gr.eh, *eT = sR + gr.et;
+    const int pl = gr.pl;
+    constexpr int Z = E::Z;
+    const T *sinfo = sR + gr.info;
     T *lofff = offf + (tid - c) * BS, *loffb = offb + (tid - c) * BS;  // this line's chunk offsets
-    const T ih = (T)d.inv_h, beta = (T)d.beta;
+    const T ih = sizeof(T) == 4 ? (T)gr.ihf : (T)gr.ih, beta = sizeof(T) == 4 ? (T)gr.betaf : (T)gr.beta;
     // segment of lanes that evaluates a line end: the whole warp for Tl >= 32, else the line
     const int S = Tl < 32 ? Tl : 32;
     const int ls = c % S;                 // lane index within the segment
@@ -752,8 +820,8 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
     constexpr int NA = (BS == 2) ? MM + 2 : 3 * MM;
     T aw[NA];     // CFD: 3 alpha / h at nodes jb-1 .. jb+MM;  MFD: alpha at the chunk's cells
     T Y[MM][BS];  // r, then y, then x
-    const int jb = g.first + c * MM;      // CFD: first node of the chunk
-    const int cb = g.first + 3 * c * MM;  // MFD: first cell of the chunk
+    const int jb = gr.mid + c * MM;      // CFD: first node of the chunk
+    const int cb = gr.mid + 3 * c * MM;  // MFD: first cell of the chunk
     if (act) {
         if constexpr (BS == 2) {
             const T c3 = T(3) * ih;
@@ -789,6 +857,32 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
     auto zval = [&](bool tail, int k) -> T {
         return k < W ? sP[(tail ? opT : 0) + k] : sV[(tail ? ovT : 0) + k - W];
     };
+    // Window parts (first 2W terms) of the end-region rows HZ and DZ, known once the line is
+    // staged: computed now by threads spread over the line and kept in the line's scratch, so
+    // that at the end the end-region lanes add only the adjacent block's BS terms.
+    // Row r < NR1 belongs to the head, r >= NR1 to the tail; within an end, HZ rows come first.
+    constexpr int NR1 = E::HMAX + (BS == 3 ? E::HMAX + 2 : 0), NR = 2 * NR1;
+    T *scr = sPw + gr.scr;
+    if (line_ok) {
+        auto row_win = [&](int r) {
+            const bool tail = r >= NR1;
+            const int q = tail ? r - NR1 : r;
+            const T *row = (tail ? eT : eH) + (q < E::HMAX ? E::HZ + q * Z : E::DZ + (q - E::HMAX) * Z);
+            T a0 = T(0), a1 = T(0);
+#pragma unroll
+            for (int k = 0; k < 2 * W; k += 2) {
+                a0 += row[k] * zval(tail, k);
+                a1 += row[k + 1] * zval(tail, k + 1);
+            }
+            scr[r] = a0 + a1;
+        };
+        const int stride = Tl >= NR ? Tl / NR : 1;
+        if (stride > 1) {
+            if (c % stride == 0 && c / stride < NR) row_win(c / stride);
+        } else {
+            for (int r = c; r < NR; r += Tl) row_win(r);
+        }
+    }
     auto seg_kz = [&](bool tail, T (&out)[BS]) {
         const T *kz = (tail ? eT : eH);
 #pragma unroll
@@ -903,10 +997,10 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
 #pragma unroll
                     for (int p = 0; p < BS; ++p)
 #pragma unroll
-                        for (int q = 0; q < BS; ++q) S[p][q] -= eT[fac_e_db(g) + p * BS + q];
+                        for (int q = 0; q < BS; ++q) S[p][q] -= eT[E::DB + p * BS + q];
                 }
             }
-            mat_inv<T, BS>(S, Si[i]);
+            fac_inv<T, BS>(S, Si[i]);
             T t[BS];
             if (i == 0) {
 #pragma unroll
@@ -953,7 +1047,7 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
         if (act)
 #pragma unroll
             for (int p = 0; p < BS; ++p) lofff[c * BS + p] = Y[MM - 1][p];
-        __syncthreads();
+        workers_sync();
         if (act) win_scan<T, BS>(true, c, tact, (int)sinfo[0], sR + tact * B2, lofff, yin);
     }
     if (act) {
@@ -992,11 +1086,11 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
         }
         seg_scan<T, BS>(mp, false, Tl, xin, ssm);
     } else {
-        if (offb == offf) __syncthreads();  // one offset buffer: the forward reads are done
+        if (offb == offf) workers_sync();  // one offset buffer: the forward reads are done
         if (act)
 #pragma unroll
             for (int p = 0; p < BS; ++p) loffb[c * BS + p] = Y[0][p];
-        __syncthreads();
+        workers_sync();
         if (act) win_scan<T, BS>(false, c, tact, (int)sinfo[1], sR + 2 * tact * B2, loffb, xin);
     }
     if (act) {
@@ -1079,18 +1173,19 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
 #pragma unroll
         for (int b = 0; b < BS; ++b) xJ[b] = __shfl_sync(0xffffffffu, tail ? Y[MM - 1][b] : Y[0][b], src_lane);
         if (!line_ok) return;
-        const int m = tail ? g.tu : g.hu;
-        auto row_dot = [&](const T *row) -> T {
-            T acc = T(0);
-            for (int k = 0; k < 2 * W; ++k) acc += row[k] * zval(tail, k);
+        const int m = tail ? gr.tu : gr.hu;
+        const T *pscr = scr + (tail ? NR1 : 0);
+        // row = [window part (scratch) | adjacent block's BS terms]
+        auto row_dot = [&](const T *row, int r) -> T {
+            T acc = pscr[r];
 #pragma unroll
             for (int b = 0; b < BS; ++b) acc += row[2 * W + b] * xJ[b];
             return acc;
         };
         if constexpr (BS == 2) {
-            const int r0 = tail ? 2 * N - g.tu : 0;
+            const int r0 = tail ? 2 * N - gr.tu : 0;
             for (int q = ls; q < m; q += S) {
-                const T x = row_dot(et + fac_e_hz(g) + q * Z);
+                const T x = row_dot(et + E::HZ + q * Z, q);
                 const int i = r0 + q;
                 const bool is_g = (i == 0) || (i == 2 * N - 1) || (i % 2 == 0);
                 const int node = i == 0 ? 0 : (i == 2 * N - 1 ? N : (i + 1) / 2);
@@ -1103,75 +1198,84 @@ __device__ __forceinline__ void fac_group(int4 gr, const unsigned char *stage_ra
                 }
             }
         } else {
-            const int cell0 = tail ? N - g.tu + 1 : 1;
+            const int cell0 = tail ? N - gr.tu + 1 : 1;
             for (int q = ls; q < m; q += S) {
-                const T x = row_dot(et + fac_e_hz(g) + q * Z);
+                const T x = row_dot(et + E::HZ + q * Z, q);
                 const int cc = cell0 + q;
                 out_p(cc, T(2) * x - sP[cc], x);
                 if (cc == src_k) add_source();
             }
-            const int qb = g.first + 3 * (g.nb - 1);
-            const int jlo = tail ? qb + 1 : 0, nrow = tail ? N - qb : g.hu + 2;
+            const int qb = gr.mid + 3 * (tact * MM - 1);
+            const int jlo = tail ? qb + 1 : 0, nrow = tail ? N - qb : gr.hu + 2;
             for (int q = ls; q < nrow; q += S) {
                 const int j = jlo + q;
-                out_v(j, sV[j], beta * ih * row_dot(et + fac_e_dz(g) + q * Z));
+                out_v(j, sV[j], beta * ih * row_dot(et + E::DZ + q * Z, E::HMAX + q));
             }
         }
     };
+    __syncwarp();  // scratch rows written by other lanes (lines within one warp, no scan barrier)
     if (head_seg) seg_end(false);
     if (tail_seg) seg_end(true);
 }
 
 // ---------------------------------------------------------------------------------------
-// The kernel: persistent CTAs walk the line groups g = blockIdx.x, blockIdx.x + gridDim.x,
-// ...; with two stages thread 0 starts the copies of the next group before the current one
-// is solved.  A wait that runs out sets *fault and ends the CTA.
+// The kernel: persistent CTAs walk the line groups g = blockIdx.x, blockIdx.x + gridDim.x, ...
+// through a ring of `stages` shared-memory stages.  The last warp stages the groups: one lane
+// waits until the compute warps have released a stage (mbarrier "empty") and starts the bulk
+// copies of the next group into it (mbarrier "full").  The 15 compute warps wait for "full",
+// solve the group and release the stage.  Every wait is bounded; one that runs out sets *fault
+// and the warp carries on with the same iteration count, so no warp is left waiting at a
+// barrier and the launch ends (with garbage results and the fault flag set).
 // ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 template <typename T, int BS, int MM>
 __global__ void __launch_bounds__(kFacThreads, 1)
-line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const int4 *__restrict__ groups, int ngroups,
+line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup *__restrict__ groups, int ngroups,
                            int natural, unsigned stage_bytes, int stages, int full_scan, int *fault) {
     extern __shared__ __align__(128) unsigned char fac_smem[];
     __shared__ ScanSmem<T, BS> ssm;
-    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ __align__(8) unsigned long long full[2], empty[2];
     // chunk offsets of the windowed scans: forward and backward buffers for FP32, one for FP64
     constexpr int kBufs = sizeof(T) == 4 ? 2 : 1;
     __shared__ T offs[kBufs][kFacThreads * BS];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kFacWorkers / 32);
+        }
         mbar_fence_init();
     }
     __syncthreads();
     const bool two = stages == 2;
-    if (two && tid == 0 && (int)blockIdx.x < ngroups) fac_issue<T>(descs, groups[blockIdx.x], fac_smem, &bars[0]);
-    int it = 0;
-    bool ok = true;
-    int gi = blockIdx.x;
-    for (; gi < ngroups; gi += gridDim.x, ++it) {
-        const int st = two ? (it & 1) : 0;
-        const unsigned par = two ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1);
-        if (tid == 0) {
-            if (two) {
-                const int gn = gi + (int)gridDim.x;
-                if (gn < ngroups) fac_issue<T>(descs, groups[gn], fac_smem + (size_t)(st ^ 1) * stage_bytes, &bars[st ^ 1]);
-            } else {
-                fac_issue<T>(descs, groups[gi], fac_smem, &bars[0]);
+    if (tid >= kFacWorkers) {  // the staging warp
+        if (lane == 0) {
+            int last[2] = {-1, -1};
+            int it = 0;
+            for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x, ++it) {
+                const int st = two ? (it & 1) : 0;
+                const int use = two ? (it >> 1) : it;
+                if (use > 0 && !mbar_wait(&empty[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
+                fac_issue<T>(descs, groups + gi, fac_smem + (size_t)st * stage_bytes, &full[st]);
+                last[st] = use;
             }
+            // the last fills land before the CTA's shared memory can be released
+            for (int k = 0; k < 2; ++k)
+                if (last[k] >= 0) (void)mbar_wait(&full[k], (unsigned)(last[k] & 1));
         }
-        const bool got = mbar_wait(&bars[st], par);
-        if (!__syncthreads_and(got)) { ok = false; break; }
-        fac_group<T, BS, MM>(groups[gi], fac_smem + (size_t)st * stage_bytes, natural, full_scan, ssm, offs[0],
-                             offs[kBufs - 1]);
-        __syncthreads();
+        return;
     }
-    if (!ok && tid == 0) {
-        atomicExch(fault, 1);
-        // let copies still in flight land before the CTA's shared memory is released
+    int it = 0;
+    for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x, ++it) {
         const int st = two ? (it & 1) : 0;
-        (void)mbar_wait(&bars[st], two ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1));
-        if (two && gi + (int)gridDim.x < ngroups) (void)mbar_wait(&bars[st ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+        const int use = two ? (it >> 1) : it;
+        if (!mbar_wait(&full[st], (unsigned)(use & 1))) atomicExch(fault, 1);
+        fac_group<T, BS, MM>(fac_smem + (size_t)st * stage_bytes, natural, full_scan, ssm, offs[0], offs[kBufs - 1]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
     }
 }
 
@@ -1183,7 +1287,7 @@ cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, double *ws, 
 }
 
 template <typename T, int BS, int MM>
-cudaError_t launch_fac_inst(const LineDesc<T> *d, const int4 *groups, int ngroups, size_t stage_bytes, int stages,
+cudaError_t launch_fac_inst(const LineDesc<T> *d, const FacGroup *groups, int ngroups, size_t stage_bytes, int stages,
                             int grid, int natural, int full_scan, int *fault, cudaStream_t s) {
     auto kern = line_solve_factored_kernel<T, BS, MM>;
     const size_t dyn = (size_t)stages * stage_bytes;
@@ -1194,7 +1298,7 @@ cudaError_t launch_fac_inst(const LineDesc<T> *d, const int4 *groups, int ngroup
 }
 
 template <typename T>
-cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups, int ngroups, int variant,
+cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const FacGroup *groups, int ngroups, int variant,
                                        size_t stage_bytes, int stages, int grid, int natural, int max_reach,
                                        int *fault, cudaStream_t s) {
     if (ngroups <= 0) return cudaSuccess;
@@ -1211,9 +1315,9 @@ cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups,
 
 template cudaError_t launch_fac_precompute<float>(const LineDesc<float> *, int, double *, int *, cudaStream_t);
 template cudaError_t launch_fac_precompute<double>(const LineDesc<double> *, int, double *, int *, cudaStream_t);
-template cudaError_t launch_line_solve_factored<float>(const LineDesc<float> *, const int4 *, int, int, size_t, int,
+template cudaError_t launch_line_solve_factored<float>(const LineDesc<float> *, const FacGroup *, int, int, size_t, int,
                                                        int, int, int, int *, cudaStream_t);
-template cudaError_t launch_line_solve_factored<double>(const LineDesc<double> *, const int4 *, int, int, size_t,
+template cudaError_t launch_line_solve_factored<double>(const LineDesc<double> *, const FacGroup *, int, int, size_t,
                                                         int, int, int, int, int *, cudaStream_t);
 
 }  // namespace adi

@@ -62,6 +62,18 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
 size_t v1_scratch_words(int method, int N);
 
 // Factored solver (adi_factored.cu).
+// One line group of a launch, built on the host: lines [first, first + nl) of one simulation
+// and direction, with the geometry every thread of the CTA needs.
+// Copied into shared memory with the group's lines.
+struct alignas(16) FacGroup {
+    int first, nl, N, T;     // first descriptor, lines, cells per line, threads per line
+    int tact, hu, tu, mid;   // chunks with blocks, end-region unknowns, first middle node / cell
+    int lp, rec, eh, et;     // staged line elements, record elements, head / tail table offsets
+    int info, pl, ls, scr;   // scan-reach offset, far Dirichlet index, staged line stride, scratch offset
+    double ih, beta;         // 1/h and dt/2 of the simulation
+    float ihf, betaf, pad0, pad1;
+};
+FacGroup fac_group_of(int method, int N, int first, int nl, double inv_h, double beta);
 bool fac_supported(int method, int N, size_t esz);  // chunks fit a CTA, stage fits smem
 size_t fac_words(int method, int N);     // elements of one line's record
 int fac_chunks(int method, int N);       // threads per line
@@ -78,7 +90,7 @@ cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, double *ws, 
 // max_reach: the largest scan reach of the launch's lines (beyond the window limit the
 // kernel uses the full scan)
 template <typename T>
-cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const int4 *groups, int ngroups,
+cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const FacGroup *groups, int ngroups,
                                        int variant, size_t stage_bytes, int stages, int grid,
                                        int natural, int max_reach, int *fault, cudaStream_t s);
 
