@@ -35,18 +35,21 @@ import numpy as np
 N_SIDE = 4096
 METRIC = "ADI grid-point updates/s (batched FP32 vs plain FP64, 4096^2); p50/p99 latency"
 UNIT = "updates/s"
+REF_BUDGET_S = 90.0  # host seconds of the reference arm (warm-up + timed steps)
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=N_SIDE)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--solver", default="default", choices=["default", "line", "chunked", "factored"],
                     help="line solver of the FP32 batch (default: the library's choice)")
     return ap.parse_args()
@@ -154,6 +157,21 @@ def ncu_traffic_per_point():
     return float(d["dram_bytes_per_point"])
 
 
+def replica_throughput(local_ms, pts_per_rank, steps, device=None):
+    """Whole-job updates/s of N independent replicas: every rank advanced pts_per_rank points by
+    `steps` steps; the job's time is the slowest rank's (max over ranks).  Returns
+    (updates/s, max ms).  Single process when torch.distributed is not initialised."""
+    import torch
+
+    ws = 1
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        ws = torch.distributed.get_world_size()
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        local_ms = float(t.item())
+    return ws * pts_per_rank * steps / (local_ms / 1e3), local_ms
+
+
 def make_specs(side, steps):
     from paper_2006_07583_gb300 import workloads as wl
 
@@ -167,7 +185,9 @@ def emit(obj):
 
 def run_reference(args):
     """The oracle as it stands, timed on the host cores on the same workload.  Each step is a
-    bounded sample: one PR step of a 512-line horizontal strip of each simulation."""
+    bounded sample of it: one PR step of a horizontal strip of each simulation (full line
+    length along x, the expensive direction of the line solves), the strip height chosen from
+    a calibration step so that warm-up plus timed steps take about REF_BUDGET_S seconds."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -175,35 +195,41 @@ def run_reference(args):
     from paper_2006_07583_gb300 import workloads as wl
 
     threads = os.cpu_count() or 1
-    strip = 512
     specs = make_specs(args.side, args.steps)
-    # the strip keeps the full line length along x (the expensive direction of the line
-    # solves) and 512 cells along y
-    cases = []
-    for sp in specs:
-        su, sv, sw = wl.shapes(sp.method, sp.nx, strip)
-        c = sp.c[:su[0], :su[1]].copy()
-        cases.append((sp.method, sp.nx, strip, sp.h, sp.dt, c ** 2,
-                      np.zeros(su), np.zeros(sv), np.zeros(sw)))
-    pts = sum(nx * ny for _, nx, ny, *_ in cases)
 
-    def one():
+    def cases_for(strip):
+        out = []
+        for sp in specs:
+            su, sv, sw = wl.shapes(sp.method, sp.nx, strip)
+            c = sp.c[:su[0], :su[1]].copy()
+            out.append((sp.method, sp.nx, strip, sp.h, sp.dt, c ** 2, np.zeros(su), np.zeros(sv), np.zeros(sw)))
+        return out
+
+    def one(cases):
         for (m, nx, ny, h, dt, kap, U, V, W) in cases:
             oracle.run(m, nx, ny, h, dt, kap, U, V, W, 1, threads=threads)
 
+    # calibration: seconds per strip row of one step
+    t0 = time.perf_counter()
+    one(cases_for(16))
+    per_row = (time.perf_counter() - t0) / 16
+    strip = int(REF_BUDGET_S / max(1, args.steps + args.warmup) / max(per_row, 1e-9))
+    strip = max(16, min(512, strip))
+    cases = cases_for(strip)
+    pts = sum(nx * ny for _, nx, ny, *_ in cases)
     for _ in range(args.warmup):
-        one()
+        one(cases)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        one()
+        one(cases)
     el = time.perf_counter() - t0
     val = pts * args.steps / el
     emit({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
           "data": "synthetic",
-          "config": {"workload": "oracle sample: 512-row strips of the 4096^2 CFD+MFD seismic "
-                                 "batch", "global_batch": 2, "side": args.side,
+          "config": {"workload": "oracle sample: %d-row strips of the %d^2 CFD+MFD seismic batch"
+                                 % (strip, args.side), "global_batch": 2, "side": args.side,
                      "parallelism": "host cores"},
           "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
                            "sample": "one PR step of a %dx%d strip of each simulation per step"
@@ -288,12 +314,7 @@ def main():
     st1 = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)]
     st2 = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(K)]
     step_ms = [a + b for a, b in zip(st1, st2)]
-    total_ms = ev[0].elapsed_time(ev[2 * K])
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * pts * K / (total_ms / 1e3)
+    value, total_ms = replica_throughput(ev[0].elapsed_time(ev[2 * K]), pts, K, device="cuda")
 
     # roofline of the dominant kernel (the line-solve launch), algorithmic bytes:
     # each stage reads the carried pressure, the velocity and alpha and writes the first two
@@ -328,6 +349,8 @@ def main():
         out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3))
     if rank == 0 and not args.no_fp64:
         out["fp64_plain"] = fp64_plain(adi, args.side)
+    if rank == 0 and not args.no_serve:
+        out["serving"] = serving_leg(adi, args.serve_requests, value)
     batch.close()
     for s in sims:
         s.close()
@@ -366,6 +389,63 @@ def e2e_leg(adi, torch, sims, batch, specs, n):
     pts = sum(sp.nx * sp.ny for sp in specs)
     return {"value": pts * n / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": h2d, "steps": n}
+
+
+def serving_leg(adi, n_req, capacity):
+    """The serving loop (adi_server_*) on a seeded Poisson request stream, scaled to finish in
+    seconds: square grids log-uniform in [64, 1024], 100-1000 steps, CFD/MFD 50/50, FP32, HBM
+    budget 150 GB; arrival rate set to an offered load of 0.8 x the batched capacity measured
+    above.  Reports p50/p99 latency (submission to completion), serving throughput, and the
+    plain one-simulation-at-a-time FP64 path on the first requests of the same stream."""
+    from paper_2006_07583_gb300 import workloads as wl
+
+    probe = wl.serving_stream(n_req, 1.0, seed=3, lo=64, hi=1024, steps_lo=100, steps_hi=1000)
+    mean_work = float(np.mean([r.spec.points * r.spec.steps for r in probe]))
+    rate = 0.8 * capacity / mean_work
+    reqs = wl.serving_stream(n_req, rate, seed=3, lo=64, hi=1024, steps_lo=100, steps_hi=1000)
+    srv = adi.Server(150 << 30, precision=adi.ADI_FP32, quantum=100, max_active=64)
+    tickets = []
+    t0 = time.perf_counter()
+    nxt, running, pending = 0, 0, 0
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt].arrival <= now:
+            sp = reqs[nxt].spec
+            tickets.append(srv.submit(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, sp.steps,
+                                      source=sp.source.as_tuple()))
+            nxt += 1
+        if running or pending:
+            running, pending = srv.tick()
+        elif nxt < len(reqs):
+            time.sleep(max(0.0, min(0.01, reqs[nxt].arrival - now)))
+            running, pending = srv.tick()
+        else:
+            break
+    wall = time.perf_counter() - t0
+    lat = []
+    for t in tickets:
+        st, ts, _t0, t1 = srv.status(t)
+        lat.append(1e3 * (t1 - ts))
+    srv.close()
+    work = sum(r.spec.points * r.spec.steps for r in reqs)
+    # plain path: FP64, thread-per-line solver, one simulation at a time, on the first requests
+    n_plain = min(6, len(reqs))
+    tp = 0.0
+    for r in reqs[:n_plain]:
+        sp = r.spec
+        tq = time.perf_counter()
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP64, solver=adi.ADI_SOLVER_LINE)
+        s.set_source(*sp.source.as_tuple())
+        s.step(sp.steps)
+        s.sync()
+        s.close()
+        tp += time.perf_counter() - tq
+    plain = sum(r.spec.points * r.spec.steps for r in reqs[:n_plain]) / tp
+    return {"requests": len(reqs), "offered_rate_per_s": rate, "wall_s": wall, "value": work / wall,
+            "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "plain_fp64_one_at_a_time": {"value": plain, "unit": UNIT, "requests": n_plain},
+            "workload": "Poisson stream, sides log-uniform 64-1024, 100-1000 steps, CFD/MFD, FP32, "
+                        "150 GB budget, quantum 100 steps"}
 
 
 def fp64_plain(adi, side):

@@ -167,6 +167,56 @@ int adi_batch_half_step(adi_batch b, int stage, int write_natural);
 int adi_batch_destroy(adi_batch b);
 
 /*
+ * Serving.  A server runs simulations requested at any time on the current device:
+ * requests wait in a FIFO queue and are admitted, in order, while the device memory their
+ * state needs (adi_server_bytes) fits in the server's HBM budget and fewer than max_active
+ * are running.  Admitted simulations stay resident and advance together: adi_server_tick
+ * advances every running simulation by the same number of steps -- the server's quantum, or
+ * fewer so that none passes its requested step count -- as one batch (one kernel launch per
+ * half step and kernel variant over all their lines, adi_batch_*), then retires the finished
+ * ones (their fields are copied to host memory and their device memory is freed) and admits
+ * waiting requests into the freed budget.  The batch is re-formed whenever its membership
+ * changes.  Requests arriving while others run are thus admitted at the next tick (continuous
+ * batching).  The paper has no counterpart; the simulations themselves are the library's.
+ * A server is not thread-safe.
+ */
+typedef struct adi_server_t *adi_server;
+typedef struct {
+    int method, nx, ny;          /* as adi_create */
+    double h, dt;
+    const double *c_field;       /* host, shape of U; copied by adi_server_submit */
+    const double *u0, *v0, *w0;  /* host initial fields or NULL (zeros); copied */
+    int nsteps;                  /* steps to run, >= 0 */
+    int has_source;              /* nonzero: Ricker source (adi_set_source) below */
+    int src_i, src_j;
+    double src_amp, src_f0, src_tdelay;
+} adi_request;
+enum { ADI_REQ_PENDING = 0, ADI_REQ_RUNNING = 1, ADI_REQ_DONE = 2, ADI_REQ_FAILED = 3 };
+
+/* Device bytes the server reserves for one request: adi_state_bytes plus its share of the
+ * batch's line descriptors (0 if the configuration is invalid). */
+size_t adi_server_bytes(int method, int nx, int ny, int precision);
+/* hbm_budget: bytes the server's simulations may hold; precision: of every simulation;
+ * quantum >= 1: steps per tick at most; max_active >= 1: simultaneously running simulations. */
+int adi_server_create(adi_server *out, size_t hbm_budget, int precision, int quantum, int max_active);
+/* Queues a request (arrays are copied); *ticket identifies it.  ADI_EINVAL for an invalid
+ * request, ADI_ENOMEM if it could never fit the budget. */
+int adi_server_submit(adi_server s, const adi_request *req, int *ticket);
+/* One scheduling round (admit, advance, retire, admit); returns after the device work of the
+ * round has finished.  *n_running, *n_pending (may be NULL) report the state afterwards. */
+int adi_server_tick(adi_server s, int *n_running, int *n_pending);
+/* State of a request (ADI_REQ_*) and its times in seconds since the server was created:
+ * submission, admission and completion (negative while not reached).  Any pointer may be
+ * NULL. */
+int adi_server_status(adi_server s, int ticket, int *state, double *t_submit, double *t_start,
+                      double *t_done);
+/* Fields of a finished request (shapes as adi_read_fields; NULL skips a field). */
+int adi_server_result(adi_server s, int ticket, double *u, double *v, double *w);
+/* Device bytes currently reserved by running simulations. */
+size_t adi_server_used_bytes(adi_server s);
+int adi_server_destroy(adi_server s);
+
+/*
  * adi_step_static -- one time step (stage 1 then stage 2, no source term) of a small
  * simulation whose fields the caller keeps in device memory, computed without allocating
  * anything.  The paper has no counterpart: this is a library service for callers that must

@@ -27,6 +27,20 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
 
+
+class AdiRequest(ctypes.Structure):
+    """adi_request (include/adi.h)."""
+    _fields_ = [("method", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("h", ctypes.c_double), ("dt", ctypes.c_double),
+                ("c_field", _dp), ("u0", _dp), ("v0", _dp), ("w0", _dp),
+                ("nsteps", ctypes.c_int), ("has_source", ctypes.c_int),
+                ("src_i", ctypes.c_int), ("src_j", ctypes.c_int),
+                ("src_amp", ctypes.c_double), ("src_f0", ctypes.c_double),
+                ("src_tdelay", ctypes.c_double)]
+
+
+ADI_REQ_PENDING, ADI_REQ_RUNNING, ADI_REQ_DONE, ADI_REQ_FAILED = 0, 1, 2, 3
+
 _SIGS = {
     "adi_abi_version": ([], ctypes.c_int),
     "adi_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -53,6 +67,15 @@ _SIGS = {
     "adi_batch_destroy": ([_vp], ctypes.c_int),
     "adi_step_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                          ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "adi_server_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "adi_server_create": ([ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+                          ctypes.c_int),
+    "adi_server_submit": ([_vp, ctypes.POINTER(AdiRequest), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "adi_server_tick": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "adi_server_status": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp], ctypes.c_int),
+    "adi_server_result": ([_vp, ctypes.c_int, _dp, _dp, _dp], ctypes.c_int),
+    "adi_server_used_bytes": ([_vp], ctypes.c_size_t),
+    "adi_server_destroy": ([_vp], ctypes.c_int),
 }
 
 
@@ -224,3 +247,70 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """A serving loop on the current device (adi_server_*): FIFO admission by HBM budget,
+    admitted simulations advanced together as one batch, re-formed as they join and leave."""
+
+    def __init__(self, hbm_budget, precision=ADI_FP32, quantum=100, max_active=64):
+        h = _vp()
+        _check(lib().adi_server_create(ctypes.byref(h), int(hbm_budget), precision, int(quantum),
+                                       int(max_active)), "adi_server_create")
+        self._s = h
+        self._keep = {}
+
+    def submit(self, method, nx, ny, h, dt, c, nsteps, U=None, V=None, W=None, source=None):
+        su, sv, sw = workloads.shapes(method, nx, ny)
+        c, cp = _arr(c, su)
+        U, up = _arr(U, su)
+        V, vp = _arr(V, sv)
+        W, wp = _arr(W, sw)
+        r = AdiRequest(method=method, nx=nx, ny=ny, h=h, dt=dt, c_field=cp, u0=up, v0=vp, w0=wp,
+                       nsteps=int(nsteps), has_source=0)
+        if source is not None:
+            r.has_source = 1
+            r.src_i, r.src_j, r.src_amp, r.src_f0, r.src_tdelay = source
+        t = ctypes.c_int()
+        _check(lib().adi_server_submit(self._s, ctypes.byref(r), ctypes.byref(t)), "adi_server_submit")
+        self._keep[t.value] = (method, nx, ny)
+        return t.value
+
+    def tick(self):
+        nr, npd = ctypes.c_int(), ctypes.c_int()
+        _check(lib().adi_server_tick(self._s, ctypes.byref(nr), ctypes.byref(npd)), "adi_server_tick")
+        return nr.value, npd.value
+
+    def status(self, ticket):
+        st = ctypes.c_int()
+        ts, t0, t1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().adi_server_status(self._s, int(ticket), ctypes.byref(st), ctypes.byref(ts),
+                                       ctypes.byref(t0), ctypes.byref(t1)), "adi_server_status")
+        return st.value, ts.value, t0.value, t1.value
+
+    def result(self, ticket):
+        method, nx, ny = self._keep[ticket]
+        su, sv, sw = workloads.shapes(method, nx, ny)
+        U, V, W = np.empty(su), np.empty(sv), np.empty(sw)
+        _check(lib().adi_server_result(self._s, int(ticket), U.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
+                                       W.ctypes.data_as(_dp)), "adi_server_result")
+        return U, V, W
+
+    def used_bytes(self):
+        return int(lib().adi_server_used_bytes(self._s))
+
+    def close(self):
+        if getattr(self, "_s", None) is not None and _lib is not None:
+            _lib.adi_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_bytes(method, nx, ny, precision=ADI_FP32) -> int:
+    return int(lib().adi_server_bytes(method, nx, ny, precision))
+

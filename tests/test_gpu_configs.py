@@ -1,0 +1,139 @@
+"""GPU checks at the workloads' own sizes, where the CPU oracle is too slow to run directly.
+
+* Convergence (exact standing wave, FP64 on the GPU, dt ~ h^2): the error against the exact
+  solution falls at a rate near 4 for both schemes, as the oracle's does on coarser grids.
+* Layered seismic medium, MFD, 1001 x 1001 cells, 15 Hz Ricker source, 2000 steps: FP32 against
+  FP64 (the FP64 path matches the oracle to 1e-12 on every smaller case), relative L2 of the
+  pressure <= 1e-4.
+* A batch of many simulations of uneven sizes: each result equals the simulation run alone.
+* Full bench size (4096 x 4096, one CFD and one MFD simulation batched, FP32, the default
+  solver, the launch configuration bench.py times): one step against the FP64 thread-per-line
+  solver (an independent kernel, pinned to the oracle at small sizes), relative L2 <= 1e-4 per
+  field (the FP32 bar of the path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2006_07583_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+CFD, MFD = wl.CFD, wl.MFD
+
+
+@pytest.fixture(scope="module")
+def adi():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_07583_gb300 import adi as _adi
+
+    _adi.lib()
+    return _adi
+
+
+def _l2_rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("method", [CFD, MFD])
+def test_fp64_convergence_rate_near_4_on_gpu(adi, method):
+    Ns, errs = [32, 64, 128, 256], []
+    T = 0.25
+    for N in Ns:
+        dt = 32.0 / N ** 2
+        steps = int(round(T / dt))
+        U, V, W = wl.standing_wave(method, N, 0.0)
+        s = adi.Sim(method, N, N, 1.0 / N, dt, wl.unit_kappa(method, N, N), U, V, W, precision=adi.ADI_FP64)
+        s.step(steps)
+        G = s.read()
+        s.close()
+        Ue, _, _ = wl.standing_wave(method, N, steps * dt)
+        errs.append((1.0 / N) * np.linalg.norm(G[0] - Ue))
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+    assert all(3.6 < r < 4.6 for r in rates), (errs, rates)
+
+
+def test_mfd_1001_fp32_against_fp64_2000_steps(adi):
+    sp = wl.seismic_spec(MFD, 1001, 1001, 2000, h=5.0, seed=1)
+    out = []
+    for prec in (adi.ADI_FP32, adi.ADI_FP64):
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=prec)
+        s.set_source(*sp.source.as_tuple())
+        s.step(sp.steps)
+        out.append(s.read())
+        s.close()
+    assert np.max(np.abs(out[1][0])) > 0
+    assert _l2_rel(out[0][0], out[1][0]) <= 1e-4
+
+
+def test_many_uneven_simulations_batched_equal_alone(adi):
+    rng = np.random.default_rng(2)
+    specs = []
+    for k in range(24):
+        method = CFD if k < 12 else MFD
+        nx, ny = int(rng.integers(128, 400)), int(rng.integers(128, 400))
+        specs.append(wl.seismic_spec(method, nx, ny, 30, h=5.0, seed=int(rng.integers(1 << 30)),
+                                     speeds=wl.random_layer_speeds(rng)))
+
+    def make(sp):
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32)
+        s.set_source(*sp.source.as_tuple())
+        return s
+
+    alone = []
+    for sp in specs:
+        s = make(sp)
+        s.step(sp.steps)
+        alone.append(s.read())
+        s.close()
+    sims = [make(sp) for sp in specs]
+    b = adi.Batch(sims)
+    b.step(30)
+    b.sync()
+    for s, ref in zip(sims, alone):
+        for g, r in zip(s.read(), ref):
+            assert np.max(np.abs(g - r)) <= 1e-6 * max(np.max(np.abs(r)), 1e-30)
+    b.close()
+    for s in sims:
+        s.close()
+
+
+def test_bench_size_one_step_against_fp64_line_solver(adi):
+    side = 4096
+    rng = np.random.default_rng(7)
+    res = {}
+    for method, seed in ((CFD, 1), (MFD, 2)):
+        sp = wl.seismic_spec(method, side, side, 1, h=5.0, seed=seed)
+        su, sv, sw = wl.shapes(method, side, side)
+        # smooth random initial fields (a few low modes) with zero walls
+        (ux, uy), (vx, vy), (wx, wy) = wl.point_coords(method, side, side, 1.0 / side)
+        def smooth(x, y, k):
+            a = rng.standard_normal(3)
+            return sum(a[i] * np.outer(np.sin((i + 1) * np.pi * y), np.sin((i + k) * np.pi * x)) for i in range(3))
+        U, V, W = smooth(ux, uy, 1), smooth(vx, vy, 2), smooth(wx, wy, 3)
+        U[0, :] = U[-1, :] = 0.0; U[:, 0] = U[:, -1] = 0.0
+        res[method] = (sp, U, V, W)
+    sims = [adi.Sim(m, side, side, sp.h, sp.dt, sp.c, U, V, W, precision=adi.ADI_FP32)
+            for m, (sp, U, V, W) in res.items()]
+    for s, (sp, *_r) in zip(sims, res.values()):
+        s.set_source(*sp.source.as_tuple())
+    b = adi.Batch(sims)
+    b.step(1)
+    b.sync()
+    got = [s.read() for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    for (m, (sp, U, V, W)), g in zip(res.items(), got):
+        r = adi.Sim(m, side, side, sp.h, sp.dt, sp.c, U, V, W, precision=adi.ADI_FP64,
+                    solver=adi.ADI_SOLVER_LINE)
+        r.set_source(*sp.source.as_tuple())
+        r.step(1)
+        ref = r.read()
+        r.close()
+        for a, bb in zip(g, ref):
+            assert _l2_rel(a, bb) <= 1e-4
