@@ -1125,8 +1125,13 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
         gpo[k * spo] = val_out;
         if (uo) uo[k * snp] = val_nat;
     };
+    // Lines of at least a warp stage v' in shared memory, in place of alpha (dead once the
+    // solve is done; every thread reads alpha only at its own nodes before writing there),
+    // and leave it with one bulk copy per line; shorter lines store v' directly.
+    const bool stage_v = Tl >= 32;
+    T *sOut = sPw + 2 * Lp;
     auto out_v = [&](int j, T vin, T dv) {  // dv = beta * (D_u u*)_j
-        gvo[j * svo] = vin - T(2) * dv;
+        if (stage_v) sOut[j] = vin - T(2) * dv; else gvo[j * svo] = vin - T(2) * dv;
         if (wo) wo[j * snv] = vin - dv;
     };
     if (act) {
@@ -1184,15 +1189,22 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
         };
         if constexpr (BS == 2) {
             const int r0 = tail ? 2 * N - gr.tu : 0;
-            for (int q = ls; q < m; q += S) {
-                const T x = row_dot(et + E::HZ + q * Z, q);
-                const int i = r0 + q;
+            // one row per lane (m <= 13 < S when v' is staged): alpha is read by every lane
+            // before any lane writes v' over it
+            for (int q0 = 0; q0 < m; q0 += S) {
+                const int q = q0 + ls;
+                const bool has = q < m;
+                const int i = r0 + (has ? q : 0);
                 const bool is_g = (i == 0) || (i == 2 * N - 1) || (i % 2 == 0);
                 const int node = i == 0 ? 0 : (i == 2 * N - 1 ? N : (i + 1) / 2);
+                const T x = has ? row_dot(et + E::HZ + q * Z, q) : T(0);
+                const T al = sA[node];
+                if (stage_v) __syncwarp();
+                if (!has) continue;
                 if (is_g) {
                     out_v(node, sV[node], beta * x);
                 } else {
-                    const T ae = sA[node] * x;
+                    const T ae = al * x;
                     out_p(node, sP[node] - T(2) * ae, sP[node] - ae);
                     if (node == src_k) add_source();
                 }
@@ -1216,6 +1228,20 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     __syncwarp();  // scratch rows written by other lanes (lines within one warp, no scan barrier)
     if (head_seg) seg_end(false);
     if (tail_seg) seg_end(true);
+    if (stage_v) {
+        // every line's v' is complete in shared memory: one bulk copy per line to global
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        workers_sync();
+        if (line_ok && c == 0) {
+            const unsigned bytes = round16((unsigned)(N + 1) * (unsigned)sizeof(T));
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gvo),
+                         "r"(smem_addr(sOut)), "r"(bytes)
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            // the stage is released only after the copy has read it
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------
