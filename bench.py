@@ -145,13 +145,17 @@ def kernel_source_hash() -> str:
 
 
 def ncu_traffic_per_point():
-    """DRAM bytes per grid point per stage launch from the committed ncu summary, valid only
-    while the kernel sources are unchanged since the capture."""
-    p = os.path.join(ROOT, "profiles", "line_solve_traffic.json")
+    """DRAM bytes per grid point per stage from the committed ncu summary
+    (profiles/line_solve_traffic.txt), valid only while the kernel sources are unchanged since
+    the capture."""
+    p = os.path.join(ROOT, "profiles", "line_solve_traffic.txt")
     if not os.path.exists(p):
         return None
-    with open(p) as f:
-        d = json.load(f)
+    d = {}
+    for line in open(p):
+        if ":" in line and not line.lstrip().startswith("#"):
+            k, v = line.split(":", 1)
+            d[k.strip()] = v.strip()
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
     return float(d["dram_bytes_per_point"])
