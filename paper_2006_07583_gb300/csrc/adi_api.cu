@@ -1,12 +1,15 @@
 // adi_api.cu -- host implementation of the C ABI in include/adi.h.
 //
-// Device state of one simulation (precision T).  Every line kernel reads its lines
-// contiguously: the fields a stage reads are stored with that stage's lines as rows, and
-// the carried pressure changes layout between the stages (each stage writes it transposed).
-//   A[0]   carried pressure a^m (stage-1 input, stage-2 output), row-major U layout.
-//   A[1]   carried C (stage-1 output, stage-2 input), column-major (column j of U is
-//          contiguous, leading dimension rows_u).  Outer rows/columns of both hold the
-//          Dirichlet data.
+// Device state of one simulation (precision T).  Every line kernel reads and writes its
+// lines contiguously: the fields a stage reads are stored with that stage's lines as rows, and
+// the carried pressure changes layout between the stages through a tiled transpose after
+// each stage.
+//   A[0]   carried pressure a^m (stage-1 input), row-major U layout.
+//   A[2]   carried C as stage 1 writes it, row-major; transposed into
+//   A[1]   carried C (stage-2 input), column-major (column j of U is contiguous, leading
+//          dimension ldc).
+//   A[3]   carried a as stage 2 writes it, column-major; transposed into A[0].
+//          Outer rows/columns of all four hold the Dirichlet data.
 //   V[p]   v^m (natural), row-major V layout; W[p] w* (carried), column-major W layout.
 //          Each half step reads one copy and writes the other (ping-pong, parity p flips
 //          every step), because line kernels read stencil halos that neighbouring chunks
@@ -182,6 +185,9 @@ struct Plan {
     int fstages[2][kFacVariants] = {};    // pipeline depth (2 = prefetch)
     int fgrid[2][kFacVariants] = {};      // persistent CTAs
     int freach[2][kFacVariants] = {};     // largest scan reach of the launch's lines
+    // carried-pressure transposes after each stage, one array per member: [dir]
+    DevBuf tdesc[2];
+    int tcount[2] = {0, 0}, trows[2] = {0, 0}, tcols[2] = {0, 0};
     DevBuf fault;                            // set by a factored launch whose wait ran out
     std::map<int, cudaGraphExec_t> graphs;
 };
@@ -208,6 +214,10 @@ void plan_free(Plan &p) {
         p.ngroups[d][0] = p.ngroups[d][1] = 0;
         p.smem[d][0] = p.smem[d][1] = 0;
     }
+    for (int d = 0; d < 2; ++d) {
+        dev_free(p.tdesc[d]);
+        p.tcount[d] = p.trows[d] = p.tcols[d] = 0;
+    }
     dev_free(p.scratch);
     dev_free(p.fault);
 }
@@ -229,7 +239,7 @@ struct adi_sim {
     int precision = ADI_FP32;
     double h = 0, dt = 0;
     size_t esz = 4;
-    DevBuf A[2], V[2], W[2], alpha, alphaT, Uo, Wo, tab, sep, cold_all, clock, status;
+    DevBuf A[4], V[2], W[2], alpha, alphaT, Uo, Wo, tab, sep, cold_all, clock, status;
     int parity = 0;                           // which V/W copy is current
     int plan_base = 0;                        // parity at which the own plan was built
     std::vector<unsigned char> h_desc[2][2];  // host descriptors [parity][0 = x-lines, 1 = y-lines]
@@ -299,6 +309,34 @@ __global__ void transpose_kernel(const T *__restrict__ src, int rows, int cols, 
     }
 }
 
+// One array of a batched transpose: dst[c * ld_dst + r] = src[r * ld_src + c] for r < rows,
+// c < cols.
+struct TDesc {
+    const void *src;
+    void *dst;
+    int rows, cols, ld_src, ld_dst;
+};
+
+// Batched tiled transpose (32 x 32 tiles through shared memory); blockIdx.z picks the array.
+template <typename T>
+__global__ void transpose_batch_kernel(const TDesc *__restrict__ td) {
+    __shared__ T tile[32][33];
+    const TDesc d = td[blockIdx.z];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    if (i0 >= d.rows || j0 >= d.cols) return;  // uniform over the block
+    const T *__restrict__ src = (const T *)d.src;
+    T *__restrict__ dst = (T *)d.dst;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, j = j0 + threadIdx.x;
+        if (i < d.rows && j < d.cols) tile[r][threadIdx.x] = src[(size_t)i * d.ld_src + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r, i = i0 + threadIdx.x;
+        if (i < d.rows && j < d.cols) dst[(size_t)j * d.ld_dst + i] = tile[threadIdx.x][r];
+    }
+}
+
 int transpose(adi_sim *s, const void *src, int rows, int cols, int ld_src, void *dst, int ld_dst) {
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
     if (s->precision == ADI_FP64)
@@ -335,7 +373,8 @@ int upload(adi_sim *s, const double *host, void *dst, size_t rows, size_t cols, 
 template <typename T>
 void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector<LineDesc<T>> &cols) {
     const Geometry &g = s->g;
-    T *A0 = (T *)s->A[0].p, *A1 = (T *)s->A[1].p, *Uo = (T *)s->Uo.p, *Wo = (T *)s->Wo.p;
+    T *A0 = (T *)s->A[0].p, *A1 = (T *)s->A[1].p, *A2 = (T *)s->A[2].p, *A3 = (T *)s->A[3].p;
+    T *Uo = (T *)s->Uo.p, *Wo = (T *)s->Wo.p;
     T *Vi = (T *)s->V[par].p, *Vn = (T *)s->V[1 - par].p;
     T *Wi = (T *)s->W[par].p, *Wn = (T *)s->W[1 - par].p;
     const T *al = (const T *)s->alpha.p, *alT = (const T *)s->alphaT.p;
@@ -365,12 +404,12 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
         int i = r + 1;  // grid row of this x-line
         LineDesc<T> &d = rows[r];
         d.p = A0 + (size_t)i * g.lda;
-        d.po = A1 + i;  // C is column-major: point j of row i at A1[j * ldc + i]
+        d.po = A2 + (size_t)i * g.lda;  // C row-major; transposed into A1 after the stage
         d.alpha = al + (size_t)i * g.lda;
         d.v = Vi + (size_t)i * g.ldvp;
         d.vo = Vn + (size_t)i * g.ldvp;
         d.u_out = nullptr; d.w_out = nullptr;
-        d.sp = 1; d.sv = 1; d.spo = g.ldc; d.svo = 1; d.snp = 1; d.snv = 1;
+        d.sp = 1; d.sv = 1; d.spo = 1; d.svo = 1; d.snp = 1; d.snv = 1;
         d.N = g.nx;
         d.tab = tab + (size_t)r * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
@@ -382,13 +421,13 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
         int j = c + 1;  // grid column of this y-line
         LineDesc<T> &d = cols[c];
         d.p = A1 + (size_t)j * g.ldc;
-        d.po = A0 + j;  // a is row-major
+        d.po = A3 + (size_t)j * g.ldc;  // a column-major; transposed into A0 after the stage
         d.alpha = alT + (size_t)j * g.ldc;
         d.v = Wi + (size_t)j * g.ldwc;
         d.vo = Wn + (size_t)j * g.ldwc;
         d.u_out = Uo + j;
         d.w_out = Wo + j;
-        d.sp = 1; d.sv = 1; d.spo = g.lda; d.svo = 1; d.snp = g.ldu; d.snv = g.ldw;
+        d.sp = 1; d.sv = 1; d.spo = 1; d.svo = 1; d.snp = g.ldu; d.snv = g.ldw;
         d.N = g.ny;
         d.tab = tab + (size_t)(g.piy + c) * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
@@ -503,6 +542,28 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
             }
         }
     }
+    // the transposes of the carried pressure after each stage
+    for (int dir = 0; dir < 2 && !rc; ++dir) {
+        std::vector<TDesc> td;
+        for (adi_sim *s : members) {
+            const Geometry &g = s->g;
+            TDesc t;
+            if (dir == 0) {  // C row-major (A[2]) -> column-major (A[1])
+                t.src = s->A[2].p; t.dst = s->A[1].p;
+                t.rows = g.rows_u; t.cols = g.ldu; t.ld_src = g.lda; t.ld_dst = g.ldc;
+            } else {         // a column-major (A[3]) -> row-major (A[0])
+                t.src = s->A[3].p; t.dst = s->A[0].p;
+                t.rows = g.ldu; t.cols = g.rows_u; t.ld_src = g.ldc; t.ld_dst = g.lda;
+            }
+            p.trows[dir] = std::max(p.trows[dir], t.rows);
+            p.tcols[dir] = std::max(p.tcols[dir], t.cols);
+            td.push_back(t);
+        }
+        p.tcount[dir] = (int)td.size();
+        rc = dev_alloc(p.tdesc[dir], td.size() * sizeof(TDesc));
+        if (!rc) rc = cuda_status(cudaMemcpyAsync(p.tdesc[dir].p, td.data(), td.size() * sizeof(TDesc),
+                                                  cudaMemcpyHostToDevice, stream));
+    }
     if (!rc) rc = dev_alloc(p.fault, sizeof(int));
     if (!rc) rc = cuda_status(cudaMemsetAsync(p.fault.p, 0, sizeof(int), stream));
     if (!rc && (p.v1n[0] || p.v1n[1])) {
@@ -534,6 +595,11 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
             e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
                                              (const int4 *)p.groups[dir][m].p, p.ngroups[dir][m], m,
                                              p.smem[dir][m], nat, stream);
+    if (e == cudaSuccess && p.tcount[dir]) {
+        dim3 grid((unsigned)((p.tcols[dir] + 31) / 32), (unsigned)((p.trows[dir] + 31) / 32), (unsigned)p.tcount[dir]);
+        transpose_batch_kernel<T><<<grid, dim3(32, 8), 0, stream>>>((const TDesc *)p.tdesc[dir].p);
+        e = cudaGetLastError();
+    }
     return e;
 }
 
@@ -606,7 +672,12 @@ int run_prologue_t(adi_sim *s) {
     cudaError_t e = launch_prologue<T>(cols, s->nlines[1], nullptr, nullptr, 0, 0, (T *)tmp.p, st, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     dev_free(tmp);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    // the prologue wrote a column-major (A[3]), like a stage-2 launch
+    const Geometry &g = s->g;
+    rc = transpose(s, s->A[3].p, g.ldu, g.rows_u, g.ldc, s->A[0].p, g.lda);
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
+    return rc;
 }
 
 int prologue(adi_sim *s) {
@@ -672,9 +743,12 @@ int load_state(adi_sim *s, const double *u, const double *v, const double *w, bo
     if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nVp() * esz, cudaMemcpyDeviceToDevice, s->stream));
     if (!rc && (u || !keep_missing)) rc = upload(s, u, s->Uo.p, g.rows_u, g.ldu, g.ldu, (double *)staging.p, 1.0, 0);
     if (!rc && (w || !keep_missing)) rc = upload(s, w, s->Wo.p, g.rows_w, g.ldw, g.ldw, (double *)staging.p, 1.0, 0);
-    if (!rc) rc = cuda_status(cudaMemcpy2DAsync(s->A[0].p, g.lda * esz, s->Uo.p, g.ldu * esz, g.ldu * esz,
-                                                g.rows_u, cudaMemcpyDeviceToDevice, s->stream));
-    if (!rc) rc = transpose(s, s->Uo.p, g.rows_u, g.ldu, g.ldu, s->A[1].p, g.ldc);
+    // all four carried-pressure arrays start from u (their outer rows/columns stay the
+    // Dirichlet data: line kernels write interior lines only)
+    for (int k = 0; k <= 2 && !rc; k += 2)
+        rc = cuda_status(cudaMemcpy2DAsync(s->A[k].p, g.lda * esz, s->Uo.p, g.ldu * esz, g.ldu * esz, g.rows_u,
+                                           cudaMemcpyDeviceToDevice, s->stream));
+    for (int k = 1; k <= 3 && !rc; k += 2) rc = transpose(s, s->Uo.p, g.rows_u, g.ldu, g.ldu, s->A[k].p, g.ldc);
     for (int k = 0; k < 2 && !rc; ++k) rc = transpose(s, s->Wo.p, g.rows_w, g.ldw, g.ldw, s->W[k].p, g.ldwc);
     if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
     dev_free(staging);
@@ -726,8 +800,8 @@ size_t adi_state_bytes(int method, int nx, int ny, int precision) {
     Geometry g = make_geometry(method, nx, ny);
     size_t esz = elem_size(precision);
     size_t nl = (size_t)g.pix + g.piy;
-    // a, C, alpha, alphaT, Uo; two v copies; two w* copies and Wo
-    size_t fields = (2 * g.nA() + 2 * g.nC() + g.nU() + 2 * g.nVp() + 2 * g.nWc() + g.nW()) * esz;
+    // a and C in both layouts, alpha, alphaT, Uo; two v copies; two w* copies and Wo
+    size_t fields = (3 * g.nA() + 3 * g.nC() + g.nU() + 2 * g.nVp() + 2 * g.nWc() + g.nW()) * esz;
     size_t tab = nl * kTabLine * esz;
     size_t descs = 2 * nl * desc_size(precision);  // sim copy + plan copy
     int sv = default_solver(g, esz);
@@ -763,6 +837,8 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     int rc = ADI_OK;
     rc = dev_alloc(s->A[0], g.nA() * esz);
     if (!rc) rc = dev_alloc(s->A[1], g.nC() * esz);
+    if (!rc) rc = dev_alloc(s->A[2], g.nA() * esz);
+    if (!rc) rc = dev_alloc(s->A[3], g.nC() * esz);
     for (int k = 0; k < 2 && !rc; ++k) {
         rc = dev_alloc(s->V[k], g.nVp() * esz);
         if (!rc) rc = dev_alloc(s->W[k], g.nWc() * esz);
@@ -773,7 +849,8 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     if (!rc) rc = dev_alloc(s->Wo, g.nW() * esz);
     // padding entries are read by bulk copies and the finite check: start them at zero
     {
-        DevBuf *zb[] = {&s->A[0], &s->A[1], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha, &s->alphaT};
+        DevBuf *zb[] = {&s->A[0], &s->A[1], &s->A[2], &s->A[3], &s->V[0], &s->V[1], &s->W[0], &s->W[1],
+                        &s->alpha, &s->alphaT};
         for (DevBuf *b : zb)
             if (!rc) rc = cuda_status(cudaMemsetAsync(b->p, 0, b->bytes, s->stream));
     }
@@ -947,7 +1024,7 @@ int adi_destroy(adi_handle s) {
     if (!s) return ADI_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
     plan_free(s->plan);
-    DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
+    DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->A[2], &s->A[3], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
                       &s->alphaT, &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status};
     for (DevBuf *b : bufs) dev_free(*b);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);

@@ -1114,22 +1114,23 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     T *__restrict__ wo = natural ? d.w_out : nullptr;
     const long long spo = d.spo, svo = d.svo, snp = d.snp, snv = d.snv;
     const int src_k = d.src_k;
+    // Lines of at least a warp stage their outputs in shared memory and leave with one bulk
+    // copy per line and array: the pressure output in place of the pressure line, v' in
+    // place of alpha.  Both are dead once the solve is done, and every thread reads them only
+    // at the points it writes, before writing there.  Shorter lines store directly.
+    const bool stage_v = Tl >= 32;
+    T *sOut = sPw + 2 * Lp;
     // source term dt/2 f(t_{m+1}) added by the thread that wrote pressure point src_k
     auto add_source = [&]() {
         const long long m = *d.clock;
         const T s = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(m + 1) * d.dt));
-        gpo[src_k * spo] = gpo[src_k * spo] + s;
+        if (stage_v) sPw[src_k] += s; else gpo[src_k * spo] = gpo[src_k * spo] + s;
         if (d.advance_clock) *d.clock = m + 1;
     };
     auto out_p = [&](int k, T val_out, T val_nat) {
-        gpo[k * spo] = val_out;
+        if (stage_v) sPw[k] = val_out; else gpo[k * spo] = val_out;
         if (uo) uo[k * snp] = val_nat;
     };
-    // Lines of at least a warp stage v' in shared memory, in place of alpha (dead once the
-    // solve is done; every thread reads alpha only at its own nodes before writing there),
-    // and leave it with one bulk copy per line; shorter lines store v' directly.
-    const bool stage_v = Tl >= 32;
-    T *sOut = sPw + 2 * Lp;
     auto out_v = [&](int j, T vin, T dv) {  // dv = beta * (D_u u*)_j
         if (stage_v) sOut[j] = vin - T(2) * dv; else gvo[j * svo] = vin - T(2) * dv;
         if (wo) wo[j * snv] = vin - dv;
@@ -1229,13 +1230,17 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     if (head_seg) seg_end(false);
     if (tail_seg) seg_end(true);
     if (stage_v) {
-        // every line's v' is complete in shared memory: one bulk copy per line to global
+        // every line's outputs are complete in shared memory: one bulk copy per line and array
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         workers_sync();
         if (line_ok && c == 0) {
             const unsigned bytes = round16((unsigned)(N + 1) * (unsigned)sizeof(T));
             asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gvo),
                          "r"(smem_addr(sOut)), "r"(bytes)
+                         : "memory");
+            const unsigned pbytes = round16((unsigned)(pl + 1) * (unsigned)sizeof(T));
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gpo),
+                         "r"(smem_addr(sPw)), "r"(pbytes)
                          : "memory");
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             // the stage is released only after the copy has read it
