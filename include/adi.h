@@ -164,6 +164,15 @@ int adi_batch_sync(adi_batch b);
  * caller must issue them in that order (used to time each kernel separately).
  */
 int adi_batch_half_step(adi_batch b, int stage, int write_natural);
+/*
+ * adi_batch_set_timing -- enable != 0: every later adi_batch_half_step also records CUDA
+ * events on the batch's stream around its line-solve launches (the transpose of the carried
+ * pressure that follows them is outside).  adi_batch_solve_time synchronises the stream and
+ * returns, for stage 1 or 2, the summed milliseconds and the number of half steps recorded
+ * since the previous query, then clears the record.  Timing does not change the work done.
+ */
+int adi_batch_set_timing(adi_batch b, int enable);
+int adi_batch_solve_time(adi_batch b, int stage, double *total_ms, int *count);
 int adi_batch_destroy(adi_batch b);
 
 /*

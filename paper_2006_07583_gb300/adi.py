@@ -65,6 +65,8 @@ _SIGS = {
     "adi_batch_sync": ([_vp], ctypes.c_int),
     "adi_batch_half_step": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "adi_batch_destroy": ([_vp], ctypes.c_int),
+    "adi_batch_set_timing": ([_vp, ctypes.c_int], ctypes.c_int),
+    "adi_batch_solve_time": ([_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "adi_step_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                          ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "adi_server_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
@@ -232,6 +234,16 @@ class Batch:
 
     def sync(self):
         _check(lib().adi_batch_sync(self._b), "adi_batch_sync")
+
+    def set_timing(self, enable=True):
+        _check(lib().adi_batch_set_timing(self._b, 1 if enable else 0), "adi_batch_set_timing")
+
+    def solve_time(self, stage):
+        """(summed ms, count) of the line-solve launches of `stage` recorded since the last query."""
+        ms, n = ctypes.c_double(), ctypes.c_int()
+        _check(lib().adi_batch_solve_time(self._b, int(stage), ctypes.byref(ms), ctypes.byref(n)),
+               "adi_batch_solve_time")
+        return ms.value, n.value
 
     def half_step(self, stage, write_natural=False):
         _check(lib().adi_batch_half_step(self._b, int(stage), 1 if write_natural else 0),

@@ -260,6 +260,9 @@ struct adi_sim {
 
 struct adi_batch_t {
     std::vector<adi_sim *> sims;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev[2];  // per stage: begin/end pairs of recorded solves
+    size_t ev_used[2] = {0, 0};      // events of the pool in use
     std::vector<int> base_parity;  // members' parity when the batch was built
     int parity = 0;                // batch steps taken, mod 2
     int precision = ADI_FP32;
@@ -578,10 +581,11 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
 // One stage (dir 0: stage 1 over x-lines, dir 1: stage 2 over y-lines) of a plan at plan
 // parity q.
 template <typename T>
-cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream_t stream) {
-    cudaError_t e = cudaSuccess;
+cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream_t stream, cudaEvent_t ev0,
+                          cudaEvent_t ev1) {
+    cudaError_t e = ev0 ? cudaEventRecord(ev0, stream) : cudaSuccess;
     int nat = dir == 1 ? natural : 0;
-    if (p.v1n[dir])
+    if (e == cudaSuccess && p.v1n[dir])
         e = launch_line_solve_v1<T>((const LineDesc<T> *)p.v1d[q][dir].p, p.v1n[dir], (T *)p.scratch.p,
                                     p.scratch_stride, nat, stream);
     for (int v = 0; v < kFacVariants && e == cudaSuccess; ++v)
@@ -595,6 +599,7 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
             e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
                                              (const int4 *)p.groups[dir][m].p, p.ngroups[dir][m], m,
                                              p.smem[dir][m], nat, stream);
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, stream);
     if (e == cudaSuccess && p.tcount[dir]) {
         dim3 grid((unsigned)((p.tcols[dir] + 31) / 32), (unsigned)((p.trows[dir] + 31) / 32), (unsigned)p.tcount[dir]);
         transpose_batch_kernel<T><<<grid, dim3(32, 8), 0, stream>>>((const TDesc *)p.tdesc[dir].p);
@@ -603,9 +608,10 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
     return e;
 }
 
-cudaError_t enqueue_stage_any(const Plan &p, int q, int dir, int natural, cudaStream_t stream) {
-    return p.precision == ADI_FP64 ? enqueue_stage<double>(p, q, dir, natural, stream)
-                                   : enqueue_stage<float>(p, q, dir, natural, stream);
+cudaError_t enqueue_stage_any(const Plan &p, int q, int dir, int natural, cudaStream_t stream,
+                              cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+    return p.precision == ADI_FP64 ? enqueue_stage<double>(p, q, dir, natural, stream, ev0, ev1)
+                                   : enqueue_stage<float>(p, q, dir, natural, stream, ev0, ev1);
 }
 
 // nsteps full steps starting at plan parity q0.
@@ -1093,7 +1099,19 @@ int adi_batch_step(adi_batch b, int nsteps) {
 int adi_batch_half_step(adi_batch b, int stage, int write_natural) {
     if (!b || (stage != 1 && stage != 2)) return ADI_EINVAL;
     if (b->sticky) return b->sticky;
-    cudaError_t e = enqueue_stage_any(b->plan, b->parity, stage - 1, write_natural ? 1 : 0, b->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (b->timing) {
+        std::vector<cudaEvent_t> &pool = b->ev[stage - 1];
+        size_t &used = b->ev_used[stage - 1];
+        while (pool.size() < used + 2) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) { (void)cudaGetLastError(); return ADI_ECUDA; }
+            pool.push_back(ev);
+        }
+        e0 = pool[used]; e1 = pool[used + 1];
+        used += 2;
+    }
+    cudaError_t e = enqueue_stage_any(b->plan, b->parity, stage - 1, write_natural ? 1 : 0, b->stream, e0, e1);
     if (e != cudaSuccess) return batch_fail(b, e);
     if (stage == 2) {
         b->parity ^= 1;
@@ -1112,9 +1130,36 @@ int adi_batch_sync(adi_batch b) {
     return rc;
 }
 
+int adi_batch_set_timing(adi_batch b, int enable) {
+    if (!b) return ADI_EINVAL;
+    b->timing = enable != 0;
+    return ADI_OK;
+}
+
+int adi_batch_solve_time(adi_batch b, int stage, double *total_ms, int *count) {
+    if (!b || (stage != 1 && stage != 2)) return ADI_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e);
+    const std::vector<cudaEvent_t> &pool = b->ev[stage - 1];
+    size_t &used = b->ev_used[stage - 1];
+    double sum = 0.0;
+    for (size_t k = 0; k + 1 < used; k += 2) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, pool[k], pool[k + 1]);
+        if (e != cudaSuccess) return batch_fail(b, e);
+        sum += ms;
+    }
+    if (total_ms) *total_ms = sum;
+    if (count) *count = (int)(used / 2);
+    used = 0;
+    return ADI_OK;
+}
+
 int adi_batch_destroy(adi_batch b) {
     if (!b) return ADI_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int k = 0; k < 2; ++k)
+        for (cudaEvent_t ev : b->ev[k]) cudaEventDestroy(ev);
     plan_free(b->plan);
     for (adi_sim *s : b->sims) { s->in_batch = false; s->batch_stream = nullptr; }
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

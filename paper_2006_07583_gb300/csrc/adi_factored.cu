@@ -685,6 +685,31 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 
 __host__ __device__ inline unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
 
+// Bulk copies (shared -> global) of the staged outputs of a solved group, issued by the staging
+// lane once the compute warps have released the stage; each line's pressure output (in place of
+// its pressure line) and v' (in place of alpha).  Lines shorter than a warp were stored
+// directly by the compute warps.  Returns once the copies have read the stage.
+template <typename T>
+__device__ void fac_store_outputs(const unsigned char *stage) {
+    const FacGroup &gr = *(const FacGroup *)stage;
+    if (gr.T < 32) return;
+    const LineDesc<T> *descs = (const LineDesc<T> *)(stage + kFacGroupBytes);
+    const T *base = (const T *)(stage + fac_head_bytes(gr.nl));
+    const unsigned pbytes = round16((unsigned)(gr.pl + 1) * (unsigned)sizeof(T));
+    const unsigned vbytes = round16((unsigned)(gr.N + 1) * (unsigned)sizeof(T));
+    for (int l = 0; l < gr.nl; ++l) {
+        const T *ln = base + (size_t)l * gr.ls;
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(descs[l].po),
+                     "r"(smem_addr(ln)), "r"(pbytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(descs[l].vo),
+                     "r"(smem_addr(ln + 2 * gr.lp)), "r"(vbytes)
+                     : "memory");
+    }
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 // Thread 0: stage one line group (descriptors, then per line the pressure, velocity and alpha
 // lines and the record) into shared memory.  Every source line starts on a 16-byte boundary
 // (padded leading dimensions) and the copies, rounded up to 16 bytes, stay inside the padded
@@ -758,6 +783,7 @@ __device__ __forceinline__ void win_scan(bool forward, int c, int tact, int reac
     for (int p = 0; p < BS; ++p) z[p] = T(0);
     const int k0 = forward ? max(0, c - reach) : min(tact - 1, c + reach);
     const int n = forward ? c - k0 : k0 - c;
+#pragma unroll 4
     for (int t = 0; t < n; ++t) {
         const int k = forward ? k0 + t : k0 - t;
         T M[BS][BS];
@@ -1229,24 +1255,9 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     __syncwarp();  // scratch rows written by other lanes (lines within one warp, no scan barrier)
     if (head_seg) seg_end(false);
     if (tail_seg) seg_end(true);
-    if (stage_v) {
-        // every line's outputs are complete in shared memory: one bulk copy per line and array
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        workers_sync();
-        if (line_ok && c == 0) {
-            const unsigned bytes = round16((unsigned)(N + 1) * (unsigned)sizeof(T));
-            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gvo),
-                         "r"(smem_addr(sOut)), "r"(bytes)
-                         : "memory");
-            const unsigned pbytes = round16((unsigned)(pl + 1) * (unsigned)sizeof(T));
-            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gpo),
-                         "r"(smem_addr(sPw)), "r"(pbytes)
-                         : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-            // the stage is released only after the copy has read it
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        }
-    }
+    // staged outputs are written to global memory by the staging warp once every compute warp
+    // has released the stage; make this thread's shared-memory writes visible to those copies
+    if (stage_v) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1289,13 +1300,23 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
             for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x, ++it) {
                 const int st = two ? (it & 1) : 0;
                 const int use = two ? (it >> 1) : it;
-                if (use > 0 && !mbar_wait(&empty[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
-                fac_issue<T>(descs, groups + gi, fac_smem + (size_t)st * stage_bytes, &full[st]);
+                unsigned char *stage = fac_smem + (size_t)st * stage_bytes;
+                if (use > 0) {
+                    // the previous group of this stage is solved: write its outputs, then refill
+                    if (!mbar_wait(&empty[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
+                    fac_store_outputs<T>(stage);
+                }
+                fac_issue<T>(descs, groups + gi, stage, &full[st]);
                 last[st] = use;
             }
-            // the last fills land before the CTA's shared memory can be released
+            // the last groups of each stage: wait until solved, write their outputs
             for (int k = 0; k < 2; ++k)
-                if (last[k] >= 0) (void)mbar_wait(&full[k], (unsigned)(last[k] & 1));
+                if (last[k] >= 0) {
+                    if (!mbar_wait(&empty[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
+                    fac_store_outputs<T>(fac_smem + (size_t)k * stage_bytes);
+                }
+            // global visibility of the output copies before the CTA ends
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
         }
         return;
     }
