@@ -340,6 +340,39 @@ __global__ void transpose_batch_kernel(const TDesc *__restrict__ td) {
     }
 }
 
+// FP32 batched transpose with 64 x 64 tiles and 16-byte global accesses (16 x 16 threads, four
+// float4 rows each).  Leading dimensions are multiples of 32 elements and bases 16-byte
+// aligned, so every 4-element group that starts inside a row's leading dimension is a
+// valid aligned access; rows past `rows` load as zeros, which only ever land in the
+// destination's padding, and destination rows past `cols` are not written.
+__global__ void __launch_bounds__(256) transpose_batch64_kernel(const TDesc *__restrict__ td) {
+    __shared__ float tile[64][65];
+    const TDesc d = td[blockIdx.z];
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    if (i0 >= d.rows || j0 >= d.cols) return;  // uniform over the block
+    const float *__restrict__ src = (const float *)d.src;
+    float *__restrict__ dst = (float *)d.dst;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int j = j0 + 4 * tx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = ty + 16 * k, i = i0 + r;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < d.rows && j < d.ld_src) q = *reinterpret_cast<const float4 *>(src + (size_t)i * d.ld_src + j);
+        tile[r][4 * tx] = q.x; tile[r][4 * tx + 1] = q.y; tile[r][4 * tx + 2] = q.z; tile[r][4 * tx + 3] = q.w;
+    }
+    __syncthreads();
+    const int i = i0 + 4 * tx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int cc = ty + 16 * k, jj = j0 + cc;
+        if (jj < d.cols && i < d.ld_dst) {
+            const float4 q = make_float4(tile[4 * tx][cc], tile[4 * tx + 1][cc], tile[4 * tx + 2][cc], tile[4 * tx + 3][cc]);
+            *reinterpret_cast<float4 *>(dst + (size_t)jj * d.ld_dst + i) = q;
+        }
+    }
+}
+
 int transpose(adi_sim *s, const void *src, int rows, int cols, int ld_src, void *dst, int ld_dst) {
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
     if (s->precision == ADI_FP64)
@@ -601,8 +634,13 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
                                              p.smem[dir][m], nat, stream);
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, stream);
     if (e == cudaSuccess && p.tcount[dir]) {
-        dim3 grid((unsigned)((p.tcols[dir] + 31) / 32), (unsigned)((p.trows[dir] + 31) / 32), (unsigned)p.tcount[dir]);
-        transpose_batch_kernel<T><<<grid, dim3(32, 8), 0, stream>>>((const TDesc *)p.tdesc[dir].p);
+        if (sizeof(T) == 4) {
+            dim3 grid((unsigned)((p.tcols[dir] + 63) / 64), (unsigned)((p.trows[dir] + 63) / 64), (unsigned)p.tcount[dir]);
+            transpose_batch64_kernel<<<grid, dim3(16, 16), 0, stream>>>((const TDesc *)p.tdesc[dir].p);
+        } else {
+            dim3 grid((unsigned)((p.tcols[dir] + 31) / 32), (unsigned)((p.trows[dir] + 31) / 32), (unsigned)p.tcount[dir]);
+            transpose_batch_kernel<T><<<grid, dim3(32, 8), 0, stream>>>((const TDesc *)p.tdesc[dir].p);
+        }
         e = cudaGetLastError();
     }
     return e;
