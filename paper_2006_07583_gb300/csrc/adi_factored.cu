@@ -911,6 +911,19 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     }
     auto seg_kz = [&](bool tail, T (&out)[BS]) {
         const T *kz = (tail ? eT : eH);
+        if (S == 32) {  // one window term per lane (2W <= 32), then a warp sum
+            const int k = ls;
+            const bool has = k < 2 * W;
+            const T *zp = k < W ? sP + (tail ? opT : 0) + k : sV + (tail ? ovT : 0) + (k - W);
+            const T z = has ? *zp : T(0);
+#pragma unroll
+            for (int p = 0; p < BS; ++p) out[p] = has ? kz[p * 2 * W + k] * z : T(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int p = 0; p < BS; ++p) out[p] += __shfl_xor_sync(0xffffffffu, out[p], o);
+            return;
+        }
 #pragma unroll
         for (int p = 0; p < BS; ++p) {
             T acc = T(0);
@@ -1163,15 +1176,25 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     };
     if (act) {
         if constexpr (BS == 2) {
-            T wp[MM + 2], wa[MM + 2], wv[MM + 2];
-            load_win<T, MM + 2>(sP + jb - 1, wp);
-            load_win<T, MM + 2>(sA + jb - 1, wa);
-            load_win<T, MM + 2>(sV + jb - 1, wv);
+            // alpha at the chunk's nodes is aw / (3/h); p and v at the chunk's nodes
+            const T inv_c3 = T(1) / (T(3) * ih);
+            T wp[MM], wv[MM];
+            load_win<T, MM>(sP + jb, wp);
+            load_win<T, MM>(sV + jb, wv);
+            if (stage_v && !uo && !wo) {
 #pragma unroll
-            for (int i = 0; i < MM; ++i) {
-                const T ae = wa[i + 1] * Y[i][0];
-                out_p(jb + i, wp[i + 1] - T(2) * ae, wp[i + 1] - ae);
-                out_v(jb + i, wv[i + 1], beta * Y[i][1]);
+                for (int i = 0; i < MM; ++i) {
+                    const T ae = aw[i + 1] * inv_c3 * Y[i][0];
+                    sPw[jb + i] = wp[i] - T(2) * ae;
+                    sOut[jb + i] = wv[i] - T(2) * beta * Y[i][1];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < MM; ++i) {
+                    const T ae = aw[i + 1] * inv_c3 * Y[i][0];
+                    out_p(jb + i, wp[i] - T(2) * ae, wp[i] - ae);
+                    out_v(jb + i, wv[i], beta * Y[i][1]);
+                }
             }
             if (src_k >= jb && src_k < jb + MM) add_source();
         } else {
