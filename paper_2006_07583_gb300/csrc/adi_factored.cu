@@ -811,6 +811,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     static_assert(MM >= 2, "chunks of at least two blocks");
     using E = FacEnd<BS>;
     constexpr int W = E::W;
+    static_assert(2 * W <= 32, "a window row fits one warp");
     constexpr int B2 = BS * BS;
     const int tid = threadIdx.x, lane = tid & 31;
     const FacGroup &gr = *(const FacGroup *)stage_raw;  // staged with the lines
@@ -889,7 +890,10 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     // Row r < NR1 belongs to the head, r >= NR1 to the tail; within an end, HZ rows come first.
     constexpr int NR1 = E::HMAX + (BS == 3 ? E::HMAX + 2 : 0), NR = 2 * NR1;
     T *scr = sPw + gr.scr;
-    if (line_ok) {
+    // Lines of at least three warps: the warps other than the head and tail warps compute the
+    // rows after their local forward pass (below), while the end warps form KZ z.
+    const bool scr_help = Tl >= 96;
+    if (line_ok && !scr_help) {
         auto row_win = [&](int r) {
             const bool tail = r >= NR1;
             const int q = tail ? r - NR1 : r;
@@ -1066,6 +1070,30 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 T C[BS][BS];
                 blockC(i, C);
                 f_mm<T, BS>(Si[i], C, G);
+            }
+        }
+    }
+
+    // ---- window parts of the end-region rows by the middle warps (one row per half-warp,
+    // one or two terms per lane, then a half-warp sum) ----
+    if (scr_help && line_ok) {
+        const int tw = (tact - 1) >> 5;  // the tail warp (tact > 64, so 2 <= tw)
+        if (wl != 0 && wl != tw) {
+            const int hi = wl - 1 - (wl > tw ? 1 : 0), nh = (Tl >> 5) - 2;
+            const int half = lane >> 4, k = lane & 15;
+            for (int r0 = 2 * hi; r0 < NR; r0 += 2 * nh) {  // warp-uniform trip count
+                const int r = r0 + half;
+                const bool tail = r >= NR1;
+                const int q = tail ? r - NR1 : r;
+                T a = T(0);
+                if (r < NR) {
+                    const T *row = (tail ? eT : eH) + (q < E::HMAX ? E::HZ + q * Z : E::DZ + (q - E::HMAX) * Z);
+                    a = row[k] * zval(tail, k);
+                    if (k + 16 < 2 * W) a += row[k + 16] * zval(tail, k + 16);
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (k == 0 && r < NR) scr[r] = a;
             }
         }
     }
