@@ -1228,6 +1228,29 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
         } else {
             const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
             const T bi = beta * ih;
+            if (stage_v && !uo && !wo) {
+                // staged outputs only: no per-point branches; the velocities after the last
+                // block of the tail chunk belong to the tail region
+                const T b2 = T(2) * bi;
+#pragma unroll
+                for (int i = 0; i < MM; ++i) {
+                    const int q0 = cb + 3 * i;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) sPw[q0 + m] = T(2) * Y[i][m] - sP[q0 + m];
+                    const T xn0 = i + 1 < MM ? Y[i + 1 < MM ? i + 1 : i][0] : xin[0];
+                    const T xn1 = i + 1 < MM ? Y[i + 1 < MM ? i + 1 : i][1] : xin[1];
+                    const T xn2 = i + 1 < MM ? Y[i + 1 < MM ? i + 1 : i][2] : xin[2];
+                    const T d1 = w0 * Y[i][0] + w1 * Y[i][1] + w2 * Y[i][2] + w3 * xn0;
+                    const T d2 = w0 * Y[i][1] + w1 * Y[i][2] + w2 * xn0 + w3 * xn1;
+                    const T d3 = w0 * Y[i][2] + w1 * xn0 + w2 * xn1 + w3 * xn2;
+                    if (i + 1 < MM || !is_tail) {
+                        sOut[q0 + 1] = sV[q0 + 1] - b2 * d1;
+                        sOut[q0 + 2] = sV[q0 + 2] - b2 * d2;
+                        sOut[q0 + 3] = sV[q0 + 3] - b2 * d3;
+                    }
+                }
+                if (src_k >= cb && src_k < cb + 3 * MM) add_source();
+            } else {
 #pragma unroll
             for (int i = 0; i < MM; ++i) {
                 const int q0 = cb + 3 * i;
@@ -1245,6 +1268,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 }
             }
             if (src_k >= cb && src_k < cb + 3 * MM) add_source();
+            }
         }
     }
 
@@ -1267,6 +1291,30 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
         };
         if constexpr (BS == 2) {
             const int r0 = tail ? 2 * N - gr.tu : 0;
+            if (S == 32) {
+                // one row per lane (m <= HMAX < 32); every operand is read before xJ arrives,
+                // and alpha by every lane before any lane writes v' over it
+                const int q = ls;
+                const bool has = q < m;
+                const int i = r0 + (has ? q : 0);
+                const bool is_g = (i == 0) || (i == 2 * N - 1) || (i % 2 == 0);
+                const int node = i == 0 ? 0 : (i == 2 * N - 1 ? N : (i + 1) / 2);
+                const T *row = et + E::HZ + (has ? q : 0) * Z;
+                const T base = pscr[has ? q : 0], k0 = row[2 * W], k1 = row[2 * W + 1];
+                const T al = sA[node], vv = sV[node], pp = sP[node];
+                const T x = base + k0 * xJ[0] + k1 * xJ[1];
+                if (stage_v) __syncwarp();
+                if (has) {
+                    if (is_g) {
+                        out_v(node, vv, beta * x);
+                    } else {
+                        const T ae = al * x;
+                        out_p(node, pp - T(2) * ae, pp - ae);
+                        if (node == src_k) add_source();
+                    }
+                }
+                return;
+            }
             // one row per lane (m <= 13 < S when v' is staged): alpha is read by every lane
             // before any lane writes v' over it
             for (int q0 = 0; q0 < m; q0 += S) {
