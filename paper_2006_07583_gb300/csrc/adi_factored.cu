@@ -171,7 +171,9 @@ FacGroup fac_group_of(int method, int N, int first, int nl, double inv_h, double
     r.eh = fac_chunk_elems(g); r.et = r.eh + fac_e_stride(g);
     r.info = fac_info(g); r.pl = p_last(method, N);
     r.ls = fac_line_elems(g); r.scr = 3 * r.lp + r.rec;
-    r.ih = inv_h; r.beta = beta; r.ihf = (float)inv_h; r.betaf = (float)beta; r.pad0 = r.pad1 = 0.f;
+    r.ih = inv_h; r.beta = beta; r.ihf = (float)inv_h; r.betaf = (float)beta;
+    r.tdiv = g.T > 1 ? (unsigned)(((1ull << 32) + (unsigned long long)g.T - 1) / (unsigned long long)g.T) : 0u;
+    r.pad1 = 0;
     return r;
 }
 // Table offsets of an end region, as compile-time functions of the block size (fac_e_*).
@@ -819,7 +821,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     T *stage = (T *)(stage_raw + fac_head_bytes(gr.nl));
     const int N = gr.N, Tl = gr.T, tact = gr.tact;
     const int Lp = gr.lp, R = gr.rec;
-    const int l = tid / Tl, c = tid - l * Tl;
+    const int l = Tl > 1 ? (int)__umulhi((unsigned)tid, gr.tdiv) : tid, c = tid - l * Tl;
     const bool line_ok = l < gr.nl;
     const bool act = line_ok && c < tact;
     const int ll = line_ok ? l : 0;
@@ -835,7 +837,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     const T ih = sizeof(T) == 4 ? (T)gr.ihf : (T)gr.ih, beta = sizeof(T) == 4 ? (T)gr.betaf : (T)gr.beta;
     // segment of lanes that evaluates a line end: the whole warp for Tl >= 32, else the line
     const int S = Tl < 32 ? Tl : 32;
-    const int ls = c % S;                 // lane index within the segment
+    const int ls = c & (S - 1);           // lane index within the segment (S a power of two)
     const int sbase = lane - ls;          // first lane of the segment
     const int wl = c >> 5;                // warp index within the line (Tl >= 32)
     const bool head_seg = Tl < 32 || wl == 0;
@@ -1275,7 +1277,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     // ---- head and tail regions, evaluated by their segments ----
     auto seg_end = [&](bool tail) {
         const T *et = tail ? eT : eH;
-        const int src_lane = sbase + ((tail ? tact - 1 : 0) % S);
+        const int src_lane = sbase + ((tail ? tact - 1 : 0) & (S - 1));
         T xJ[BS];
 #pragma unroll
         for (int b = 0; b < BS; ++b) xJ[b] = __shfl_sync(0xffffffffu, tail ? Y[MM - 1][b] : Y[0][b], src_lane);
@@ -1337,14 +1339,34 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
             }
         } else {
             const int cell0 = tail ? N - gr.tu + 1 : 1;
+            const int qb = gr.mid + 3 * (tact * MM - 1);
+            const int jlo = tail ? qb + 1 : 0, nrow = tail ? N - qb : gr.hu + 2;
+            if (S == 32) {
+                // one row per lane: pressure rows on lanes 0..15 (m <= HMAX), velocity rows on
+                // lanes 16..31 (nrow <= HMAX + 2)
+                static_assert(E::HMAX + 2 <= 16, "end rows fit a half-warp");
+                const bool vel = ls >= 16;
+                const int q = vel ? ls - 16 : ls;
+                const bool has = q < (vel ? nrow : m);
+                const int qq = has ? q : 0;
+                const T x = row_dot(et + (vel ? E::DZ : E::HZ) + qq * Z, vel ? E::HMAX + qq : qq);
+                if (has) {
+                    if (vel) {
+                        out_v(jlo + qq, sV[jlo + qq], beta * ih * x);
+                    } else {
+                        const int cc = cell0 + qq;
+                        out_p(cc, T(2) * x - sP[cc], x);
+                        if (cc == src_k) add_source();
+                    }
+                }
+                return;
+            }
             for (int q = ls; q < m; q += S) {
                 const T x = row_dot(et + E::HZ + q * Z, q);
                 const int cc = cell0 + q;
                 out_p(cc, T(2) * x - sP[cc], x);
                 if (cc == src_k) add_source();
             }
-            const int qb = gr.mid + 3 * (tact * MM - 1);
-            const int jlo = tail ? qb + 1 : 0, nrow = tail ? N - qb : gr.hu + 2;
             for (int q = ls; q < nrow; q += S) {
                 const int j = jlo + q;
                 out_v(j, sV[j], beta * ih * row_dot(et + E::DZ + q * Z, E::HMAX + q));

@@ -71,7 +71,9 @@ struct alignas(16) FacGroup {
     int lp, rec, eh, et;     // staged line elements, record elements, head / tail table offsets
     int info, pl, ls, scr;   // scan-reach offset, far Dirichlet index, staged line stride, scratch offset
     double ih, beta;         // 1/h and dt/2 of the simulation
-    float ihf, betaf, pad0, pad1;
+    float ihf, betaf;        // the same in FP32
+    unsigned tdiv;           // ceil(2^32 / T) (0 for T = 1): thread / T = umulhi(thread, tdiv)
+    int pad1;
 };
 FacGroup fac_group_of(int method, int N, int first, int nl, double inv_h, double beta);
 bool fac_supported(int method, int N, size_t esz);  // chunks fit a CTA, stage fits smem
