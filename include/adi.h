@@ -97,6 +97,22 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
 int adi_set_solver(adi_handle sim, int solver);
 int adi_get_solver(adi_handle sim);
 
+/*
+ * adi_autotune -- picks the line solver of a handle by measurement.  Every solver the
+ * configuration supports (ADI_SOLVER_FACTORED, _CHUNKED, _LINE: the chunk-parallel solves and
+ * the thread-per-line Thomas-style elimination) runs `trials` steps (rounded up to an even
+ * count, after as many untimed ones) on the handle's own state, timed with CUDA events on its
+ * stream, and the fastest is kept.  The carried state, the natural fields, the step clock and
+ * the parity are saved on the device first and restored afterwards, so the fields read
+ * exactly as before the call.  ms_per_step (NULL, or 3 entries indexed by adi_solver)
+ * receives each solver's time per step, -1 for one the configuration cannot use; *chosen
+ * (may be NULL) the winner.  Results are cached per (method, nx, ny, precision) for the
+ * process: a cached configuration is switched to its solver without timing unless force != 0.
+ * Errors: ADI_EINVAL (trials < 1), ADI_EBUSY inside a batch, ADI_ENOMEM if the save buffer
+ * (the size of the simulation's fields) cannot be allocated -- the handle is then unchanged.
+ */
+int adi_autotune(adi_handle sim, int trials, int force, int *chosen, double *ms_per_step);
+
 /* Device bytes adi_create allocates for this configuration with its default solver (0 if
  * invalid); transient staging buffers are not included. */
 size_t adi_state_bytes(int method, int nx, int ny, int precision);

@@ -52,6 +52,7 @@ _SIGS = {
     "adi_set_stream": ([_vp, _vp], ctypes.c_int),
     "adi_set_solver": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_get_solver": ([_vp], ctypes.c_int),
+    "adi_autotune": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp], ctypes.c_int),
     "adi_step": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_sync": ([_vp], ctypes.c_int),
     "adi_read_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
@@ -169,6 +170,15 @@ class Sim:
     @property
     def solver(self):
         return lib().adi_get_solver(self._h)
+
+    def autotune(self, trials=2, force=False):
+        """adi_autotune: times every usable solver on this simulation's own state (restored
+        afterwards) and keeps the fastest.  Returns (chosen solver, {solver: ms per step})."""
+        chosen = ctypes.c_int(-1)
+        ms = (ctypes.c_double * 3)()
+        _check(lib().adi_autotune(self._h, int(trials), 1 if force else 0, ctypes.byref(chosen), ms),
+               "adi_autotune")
+        return chosen.value, {k: ms[k] for k in range(3) if ms[k] >= 0}
 
     def step(self, n=1):
         _check(lib().adi_step(self._h, int(n)), "adi_step")

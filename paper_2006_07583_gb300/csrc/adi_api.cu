@@ -28,6 +28,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -934,6 +936,129 @@ int adi_set_solver(adi_handle s, int solver) {
 }
 
 int adi_get_solver(adi_handle s) { return s ? s->solver : -1; }
+
+}  // extern "C"
+
+namespace {
+
+// Solver choices measured by adi_autotune, per (method, nx, ny, precision).
+struct TuneResult {
+    int solver = ADI_SOLVER_LINE;
+    double ms[3] = {-1.0, -1.0, -1.0};
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, TuneResult> g_tune;
+
+// The device state a step changes: carried and natural fields and the step clock.
+int state_parts(adi_sim *s, DevBuf **parts) {
+    DevBuf *list[] = {&s->A[0], &s->A[1], &s->A[2], &s->A[3], &s->V[0], &s->V[1],
+                      &s->W[0], &s->W[1], &s->Uo, &s->Wo, &s->clock};
+    int n = 0;
+    for (DevBuf *b : list) parts[n++] = b;
+    return n;
+}
+// Copies the step state into (save = true) or out of one device buffer, on the sim's stream.
+int copy_state(adi_sim *s, DevBuf &buf, bool save) {
+    DevBuf *parts[16];
+    const int n = state_parts(s, parts);
+    size_t total = 0;
+    for (int k = 0; k < n; ++k) total += (parts[k]->bytes + 255) & ~(size_t)255;
+    if (save) {
+        int rc = dev_alloc(buf, total);
+        if (rc) return rc;
+    }
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        unsigned char *snap = (unsigned char *)buf.p + off;
+        cudaError_t e = save ? cudaMemcpyAsync(snap, parts[k]->p, parts[k]->bytes, cudaMemcpyDeviceToDevice, s->stream)
+                             : cudaMemcpyAsync(parts[k]->p, snap, parts[k]->bytes, cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        off += (parts[k]->bytes + 255) & ~(size_t)255;
+    }
+    return cuda_status(cudaStreamSynchronize(s->stream));
+}
+
+// Time per step of the sim's current solver: an untimed run of n steps (graph capture
+// included), then n timed steps between two events on the sim's stream.
+int time_steps(adi_sim *s, int n, double *ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int rc = cuda_status(e);
+    if (!rc) rc = adi_step(s, n);
+    if (!rc) rc = cuda_status(cudaEventRecord(e0, s->stream));
+    if (!rc) rc = adi_step(s, n);
+    if (!rc) rc = cuda_status(cudaEventRecord(e1, s->stream));
+    if (!rc) rc = adi_sync(s);
+    float t = 0.f;
+    if (!rc) rc = cuda_status(cudaEventElapsedTime(&t, e0, e1));
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!rc) *ms = (double)t / n;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_per_step) {
+    if (!s || trials < 1) return ADI_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (s->in_batch) return ADI_EBUSY;
+    const auto key = std::make_tuple(s->g.method, s->g.nx, s->g.ny, s->precision);
+    TuneResult res;
+    bool cached = false;
+    if (!force) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) { res = it->second; cached = true; }
+    }
+    int rc = ADI_OK;
+    if (!cached) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return s->sticky = cuda_status(e);
+        DevBuf snap;
+        rc = copy_state(s, snap, true);
+        if (rc) { dev_free(snap); return rc == ADI_ENOMEM ? ADI_ENOMEM : (s->sticky = rc); }
+        const int parity0 = s->parity, solver0 = s->solver;
+        const long long steps0 = s->steps;
+        const int n = trials + (trials & 1);  // even: both runs start at the same parity
+        double best = 0.0;
+        res.solver = -1;
+        const int order[3] = {ADI_SOLVER_FACTORED, ADI_SOLVER_CHUNKED, ADI_SOLVER_LINE};
+        for (int k = 0; k < 3 && !rc; ++k) {
+            const int sv = order[k];
+            if ((sv == ADI_SOLVER_FACTORED && !factored_ok(s->g, s->esz)) ||
+                (sv == ADI_SOLVER_CHUNKED && !chunked_ok(s->g, s->esz)))
+                continue;
+            rc = adi_set_solver(s, sv);
+            double ms = 0.0;
+            if (!rc) rc = time_steps(s, n, &ms);
+            // every candidate starts from the saved state
+            if (!rc) rc = copy_state(s, snap, false);
+            if (rc) break;
+            s->parity = parity0;
+            s->steps = steps0;
+            res.ms[sv] = ms;
+            if (res.solver < 0 || ms < best) { best = ms; res.solver = sv; }
+        }
+        if (rc) {
+            dev_free(snap);
+            return s->sticky = rc;
+        }
+        dev_free(snap);
+        if (res.solver < 0) res.solver = solver0;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = res;
+    }
+    rc = adi_set_solver(s, res.solver);
+    if (rc) return rc;
+    if (chosen) *chosen = res.solver;
+    if (ms_per_step)
+        for (int k = 0; k < 3; ++k) ms_per_step[k] = res.ms[k];
+    return ADI_OK;
+}
 
 int adi_set_stream(adi_handle s, void *stream) {
     if (!s) return ADI_EINVAL;
