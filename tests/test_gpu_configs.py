@@ -10,6 +10,9 @@
   solver, the launch configuration bench.py times): one step against the FP64 thread-per-line
   solver (an independent kernel, pinned to the oracle at small sizes), relative L2 <= 1e-4 per
   field (the FP32 bar of the path).
+* The batched configuration at full scale (256 simulations, sides 128-1024, 500 steps).
+* The FP64 refinement ladder to N = 512 (CFD) and 1024 (MFD), and the 8192 x 8192 FP32
+  heterogeneous run (one step against the FP64 thread-per-line solver).
 """
 import math
 
@@ -137,3 +140,108 @@ def test_bench_size_one_step_against_fp64_line_solver(adi):
         r.close()
         for a, bb in zip(g, ref):
             assert _l2_rel(a, bb) <= 1e-4
+
+
+def test_batched_256_simulations_at_config_scale(adi):
+    """The batched configuration at full scale: 256 simulations (128 CFD + 128 MFD), sides
+    uniform in [128, 1024], seeded layered media, 500 steps, one batch (graph-captured launches
+    per half-step).  Each result equals the same simulation run alone (1e-6 relative: the same
+    kernels on the same lines).  Sampled MFD simulations match the FP64 path within the FP32
+    bar after the 500 steps.  The CFD scheme's spatial operator has growing modes (App. A
+    closures; see test_oracle_stability.py), which the source excites and which amplify FP32
+    roundoff by about 8 % a step at this time step: sampled CFD simulations are compared with
+    FP64 over the first 30 steps, where that amplification stays below the bar."""
+    specs = wl.batch_specs(256, 128, 1024, 500, seed=2)
+
+    def make(sp, prec=0):
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=prec)
+        s.set_source(*sp.source.as_tuple())
+        return s
+
+    sims = [make(sp) for sp in specs]
+    b = adi.Batch(sims)
+    b.step(500)
+    b.sync()
+    got = [s.read() for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    for sp, g in zip(specs, got):
+        s = make(sp)
+        s.step(sp.steps)
+        ref = s.read()
+        s.close()
+        for a, r in zip(g, ref):
+            assert np.max(np.abs(a - r)) <= 1e-6 * max(np.max(np.abs(r)), 1e-30)
+    for k in (128, 200, 255):  # MFD
+        s = make(specs[k], adi.ADI_FP64)
+        s.step(specs[k].steps)
+        ref = s.read()
+        s.close()
+        assert np.max(np.abs(ref[0])) > 0
+        assert _l2_rel(got[k][0], ref[0]) <= 1e-4
+    for k in (0, 77, 127):  # CFD, 30 steps
+        res = []
+        for prec in (adi.ADI_FP32, adi.ADI_FP64):
+            s = make(specs[k], prec)
+            s.step(30)
+            res.append(s.read())
+            s.close()
+        assert np.max(np.abs(res[1][0])) > 0
+        assert _l2_rel(res[0][0], res[1][0]) <= 1e-4
+
+
+@pytest.mark.parametrize("method,top", [(CFD, 512), (MFD, 1024)])
+def test_fp64_convergence_ladder(adi, method, top):
+    """Grid-refinement ladder in FP64 on the GPU, N = 64 .. top, dt = 32 h^2, T = 0.25 (2048
+    steps at N = 512, 8192 at N = 1024).  Rates are fitted on the levels whose error is above
+    1e3 x a roundoff estimate (1e-16 x steps x max|u|); each such rate lies in (3.6, 4.6).
+    CFD stops at 512: its growing modes (test_oracle_stability.py) amplify FP64 roundoff over
+    the 8192 steps of N = 1024 to about 3e-5, far above the truncation error there."""
+    Ns = [n for n in (64, 128, 256, 512, 1024) if n <= top]
+    errs, floors = [], []
+    T = 0.25
+    for N in Ns:
+        dt = 32.0 / N ** 2
+        steps = int(round(T / dt))
+        U, V, W = wl.standing_wave(method, N, 0.0)
+        s = adi.Sim(method, N, N, 1.0 / N, dt, wl.unit_kappa(method, N, N), U, V, W, precision=adi.ADI_FP64)
+        s.step(steps)
+        G = s.read()
+        s.close()
+        Ue, _, _ = wl.standing_wave(method, N, steps * dt)
+        errs.append((1.0 / N) * np.linalg.norm(G[0] - Ue))
+        floors.append(1e3 * 1e-16 * steps * np.max(np.abs(Ue)))
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i])
+             for i in range(len(Ns) - 1) if errs[i + 1] > floors[i + 1]]
+    assert len(rates) >= 3, (errs, floors)
+    assert all(3.6 < r < 4.6 for r in rates), (errs, rates)
+
+
+@pytest.mark.parametrize("method", [CFD, MFD])
+def test_8192_fp32_heterogeneous_one_step_against_fp64_line_solver(adi, method):
+    """The 8192 x 8192 FP32 heterogeneous run (layered medium, centre Ricker; lines this long
+    take the chunked solver): smooth random fields advanced one step, against the FP64
+    thread-per-line solver on the same inputs, relative L2 <= 1e-4 per field."""
+    side = 8192
+    rng = np.random.default_rng(8 + method)
+    sp = wl.seismic_spec(method, side, side, 1, h=5.0, seed=3 + method)
+    (ux, uy), (vx, vy), (wx, wy) = wl.point_coords(method, side, side, 1.0 / side)
+
+    def smooth(x, y, k):
+        a = rng.standard_normal(3)
+        return sum(a[i] * np.outer(np.sin((i + 1) * np.pi * y), np.sin((i + k) * np.pi * x)) for i in range(3))
+
+    U, V, W = smooth(ux, uy, 1), smooth(vx, vy, 2), smooth(wx, wy, 3)
+    U[0, :] = U[-1, :] = 0.0
+    U[:, 0] = U[:, -1] = 0.0
+    out = []
+    for prec, solver in ((adi.ADI_FP32, None), (adi.ADI_FP64, adi.ADI_SOLVER_LINE)):
+        kw = {} if solver is None else {"solver": solver}
+        s = adi.Sim(method, side, side, sp.h, sp.dt, sp.c, U, V, W, precision=prec, **kw)
+        s.set_source(*sp.source.as_tuple())
+        s.step(1)
+        out.append(s.read())
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert _l2_rel(a, b) <= 1e-4
