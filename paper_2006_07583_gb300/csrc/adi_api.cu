@@ -158,8 +158,8 @@ size_t v1_words(const Geometry &g) {
     return std::max(v1_scratch_words(g.method, g.nx), v1_scratch_words(g.method, g.ny));
 }
 
-// Measured on GB300 at 4096^2 (FP32, one CFD and one MFD simulation batched): factored
-// 1.8 ms per step, chunked 3.2 ms, thread per line 30 ms.
+// The factored solver where it applies (adi_autotune measured it fastest from 128^2 to 8192^2
+// on GB300), else the chunked one, else one thread per line.
 int default_solver(const Geometry &g, size_t esz) {
     if (factored_ok(g, esz)) return ADI_SOLVER_FACTORED;
     if (chunked_ok(g, esz)) return ADI_SOLVER_CHUNKED;
@@ -507,12 +507,25 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                 int first = (int)(fdv[0][dir].size() / dsz);
                 int n = s->nlines[dir];
                 int N = dir == 0 ? s->g.nx : s->g.ny;
-                int nl = fac_lines_per_cta(s->g.method, N, esz);
                 int v = fac_variant(s->g.method, N);
-                for (int st = 0; st < n; st += nl) {
-                    int cnt = std::min(nl, n - st);
-                    fgr[dir][v].push_back(fac_group_of(s->g.method, N, first + st, cnt, 1.0 / s->h, 0.5 * s->dt));
-                    p.fstage[dir][v] = std::max(p.fstage[dir][v], fac_stage_bytes(s->g.method, N, cnt, esz));
+                if (fac_split_line(s->g.method, N)) {
+                    // lines longer than a CTA's chunks: sub-lines with a halo of the scan reach
+                    FacGroup sub[kFacMaxSplit];
+                    for (int st = 0; st < n; ++st) {
+                        size_t sb = 0;
+                        const int k = fac_split_groups(s->g.method, N, first + st, std::max(1, s->fac_reach),
+                                                       1.0 / s->h, 0.5 * s->dt, esz, sub, &sb);
+                        if (k == 0) return ADI_ENOTSUP;
+                        fgr[dir][v].insert(fgr[dir][v].end(), sub, sub + k);
+                        p.fstage[dir][v] = std::max(p.fstage[dir][v], sb);
+                    }
+                } else {
+                    int nl = fac_lines_per_cta(s->g.method, N, esz);
+                    for (int st = 0; st < n; st += nl) {
+                        int cnt = std::min(nl, n - st);
+                        fgr[dir][v].push_back(fac_group_of(s->g.method, N, first + st, cnt, 1.0 / s->h, 0.5 * s->dt));
+                        p.fstage[dir][v] = std::max(p.fstage[dir][v], fac_stage_bytes(s->g.method, N, cnt, esz));
+                    }
                 }
                 p.freach[dir][v] = std::max(p.freach[dir][v], s->fac_reach);
                 for (int q = 0; q < 2; ++q) {
@@ -772,6 +785,11 @@ int setup_solver(adi_sim *s) {
     if (!rc) rc = s->precision == ADI_FP64 ? run_precompute<double>(s) : run_precompute<float>(s);
     if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
     s->plan_base = s->parity;
+    // a split line whose scan reach exceeds the halo a sub-line can take: use the chunked solver
+    if (rc == ADI_ENOTSUP && s->solver == ADI_SOLVER_FACTORED && chunked_ok(s->g, s->esz)) {
+        s->solver = ADI_SOLVER_CHUNKED;
+        return setup_solver(s);
+    }
     return rc;
 }
 

@@ -34,6 +34,8 @@
 // whose reach exceeds kFacMaxReach use the full log-depth scan of affine maps instead.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "adi_internal.h"
 #include "adi_line.cuh"
 #include "adi_ops.cuh"
@@ -62,9 +64,19 @@ __host__ __device__ inline int fac_mm(int method, int N) {
     if (method == kCFD) return 9;
     return line_shape(kMFD, N).nb <= 2 * kFacMaxT ? 2 : 3;
 }
-// Kernel variant (one compiled instance per chunk length and method).
+// Threads a whole line needs (see fac_geom): a power of two up to 32, else a multiple of 32.
+__host__ __device__ inline int fac_geom_T(int method, int N) {
+    const int tact = line_shape(method, N).nb / fac_mm(method, N);
+    if (tact > 32) return (tact + 31) & ~31;
+    int T = 1;
+    while (T < tact) T <<= 1;
+    return T;
+}
+// Kernel variant (one compiled instance per chunk length and method, and for split lines).
 __host__ __device__ inline int fac_variant_of(int method, int N) {
-    return method == kCFD ? 0 : (fac_mm(method, N) == 2 ? 1 : 2);
+    const bool split = fac_geom_T(method, N) > kFacMaxT;
+    if (method == kCFD) return split ? 3 : 0;
+    return fac_mm(method, N) == 2 ? 1 : (split ? 4 : 2);
 }
 // End windows: p[op .. op+win) and v[ov .. ov+win); hmax bounds the eliminated unknowns of
 // one end (base head/tail plus half of at most MM-1 remainder blocks).
@@ -111,9 +123,12 @@ __host__ __device__ inline int fac_e_db(const FacGeom &g) {
     return fac_e_dz(g) + (g.method == kMFD ? (g.hmax + 2) * fac_zlen(g) : 0);
 }
 __host__ __device__ inline int fac_e_stride(const FacGeom &g) { return (fac_e_db(g) + g.bs * g.bs + 3) & ~3; }
-// Record of one line: S_first, F_c, H_c (tact blocks each), the head and tail tables, then
-// four values: the forward and backward reach of the windowed scans.
-__host__ __device__ inline int fac_chunk_elems(const FacGeom &g) { return (3 * g.tact * g.bs * g.bs + 3) & ~3; }
+// Record of one line: S_first, F_c, H_c (tact blocks each, every part padded to a multiple of
+// four elements so that each starts on a 16-byte boundary), the head and tail tables, then four
+// values: the forward and backward reach of the windowed scans.
+__host__ __device__ inline int fac_ru4(int x) { return (x + 3) & ~3; }
+__host__ __device__ inline int fac_part(const FacGeom &g) { return fac_ru4(g.tact * g.bs * g.bs); }
+__host__ __device__ inline int fac_chunk_elems(const FacGeom &g) { return 3 * fac_part(g); }
 __host__ __device__ inline int fac_info(const FacGeom &g) { return fac_chunk_elems(g) + 2 * fac_e_stride(g); }
 __host__ __device__ inline int fac_rec(const FacGeom &g) { return fac_info(g) + 4; }
 // Elements of one staged line array (pressure, velocity or alpha), a multiple of four.
@@ -152,29 +167,104 @@ int fac_lines_per_cta(int method, int N, size_t esz) {
     while (nl > 1 && fac_stages_for(fac_stage_bytes(method, N, nl, esz), esz) < 2) --nl;
     return nl;
 }
+bool fac_split_line(int method, int N) { return fac_geom(method, N).T > kFacMaxT; }
 bool fac_supported(int method, int N, size_t esz) {
     const FacGeom g = fac_geom(method, N);
-    if (g.tact < 1 || g.T > kFacMaxT) return false;
+    if (g.tact < 1) return false;
     if (g.hu > g.hmax || g.tu > g.hmax) return false;
+    if (g.T > kFacMaxT) {  // split into sub-lines (for the largest halo a split line accepts)
+        FacGroup tmp[kFacMaxSplit];
+        size_t sb = 0;
+        return fac_split_groups(method, N, 0, kFacSplitMaxHalo, 1.0, 1.0, esz, tmp, &sb) > 0;
+    }
     return fac_stages_for(fac_stage_bytes(method, N, 1, esz), esz) > 0;
 }
 size_t fac_words(int method, int N) { return (size_t)fac_rec(fac_geom(method, N)); }
 int fac_chunks(int method, int N) { return fac_geom(method, N).T; }
 int fac_variant(int method, int N) { return fac_variant_of(method, N); }
 size_t fac_ws_doubles() { return kFacWs; }
+static unsigned fac_tdiv(int T) {
+    return T > 1 ? (unsigned)(((1ull << 32) + (unsigned long long)T - 1) / (unsigned long long)T) : 0u;
+}
 FacGroup fac_group_of(int method, int N, int first, int nl, double inv_h, double beta) {
     const FacGeom g = fac_geom(method, N);
-    FacGroup r;
+    FacGroup r{};
     r.first = first; r.nl = nl; r.N = N; r.T = g.T;
     r.tact = g.tact; r.hu = g.hu; r.tu = g.tu; r.mid = g.first;
-    r.lp = fac_lp(N); r.rec = fac_rec(g);
+    r.lp = fac_lp(N); r.part = fac_part(g);
     r.eh = fac_chunk_elems(g); r.et = r.eh + fac_e_stride(g);
     r.info = fac_info(g); r.pl = p_last(method, N);
-    r.ls = fac_line_elems(g); r.scr = 3 * r.lp + r.rec;
+    r.ls = fac_line_elems(g); r.scr = 3 * r.lp + fac_rec(g);
     r.ih = inv_h; r.beta = beta; r.ihf = (float)inv_h; r.betaf = (float)beta;
-    r.tdiv = g.T > 1 ? (unsigned)(((1ull << 32) + (unsigned long long)g.T - 1) / (unsigned long long)g.T) : 0u;
-    r.pad1 = 0;
+    r.tdiv = fac_tdiv(g.T);
+    r.c0 = 0; r.lo = 0; r.pn = r.pl + 1; r.vn = N + 1;
+    r.own = (g.tact << 9) | kFacOwnHead | kFacOwnTail;
+    r.sp0 = 0; r.sp1 = r.pl + 1; r.sv0 = 0; r.sv1 = N + 1;
     return r;
+}
+
+// Sub-lines of a line with more chunks than a CTA has threads.  Sub-line i owns the chunks
+// [tact i / K, tact (i+1) / K) and also solves `halo` (rounded so that its first chunk is a
+// multiple of four: the record parts it stages then start on 16-byte boundaries) chunks on
+// each interior side.  The windowed scans of its owned chunks reach at most `halo` chunks, all
+// inside its range; the halo chunks' own scan values are truncated at the range's ends and
+// their outputs are not written.  Staged elements cover every stencil read of the range; the
+// owned outputs are stored by bulk copies on 4-element-aligned spans and, at the ragged ends
+// of a span, by the threads that compute them.
+int fac_split_groups(int method, int N, int first, int halo, double inv_h, double beta, size_t esz,
+                     FacGroup *out, size_t *stage_bytes) {
+    const FacGeom g = fac_geom(method, N);
+    if (g.tact < 1 || g.hu > g.hmax || g.tu > g.hmax || halo < 1 || halo > kFacSplitMaxHalo) return 0;
+    const int B2 = g.bs * g.bs, pl = p_last(method, N);
+    const int per = method == kCFD ? g.mm : 3 * g.mm;  // nodes (CFD) or cells (MFD) per chunk
+    const int vsh = method == kCFD ? 0 : 1;             // MFD: a chunk's velocities start one after its cells
+    int K = 2;
+    while (K <= kFacMaxSplit && (g.tact + K - 1) / K + 2 * halo + 3 > kFacMaxT) ++K;
+    if (K > kFacMaxSplit) return 0;
+    size_t smax = 0;
+    for (int i = 0; i < K; ++i) {
+        const int s0 = (int)((long long)g.tact * i / K), s1 = (int)((long long)g.tact * (i + 1) / K);
+        const bool head = i == 0, tail = i == K - 1;
+        const int c0 = head ? 0 : ((s0 - halo) & ~3);
+        const int c1 = tail ? g.tact : std::min(g.tact, s1 + halo);
+        const int tl = c1 - c0;
+        if (c0 < 0 || tl > kFacMaxT || tl <= 64) return 0;
+        FacGroup r{};
+        r.first = first; r.nl = 1; r.N = N;
+        r.tact = tl; r.T = (tl + 31) & ~31;
+        r.hu = g.hu; r.tu = g.tu; r.mid = g.first;
+        // staged elements [lo, hi): a CFD chunk reads nodes jb-1 .. jb+mm, an MFD chunk cells
+        // cb .. cb+3mm-1 and velocities cb-2 .. cb+3mm
+        const int lo = head ? 0 : ((g.first + c0 * per - 2) & ~3);
+        const int hp = tail ? pl + 1 : g.first + c1 * per + 1;
+        const int hv = tail ? N + 1 : g.first + c1 * per + 1;
+        r.lo = lo; r.pn = hp - lo; r.vn = hv - lo;
+        r.lp = fac_ru4(r.pn > r.vn ? r.pn : r.vn);
+        const int part = fac_ru4(tl * B2), es = fac_e_stride(g);
+        r.part = part;
+        int off = 3 * part;
+        r.eh = head ? off : -1;
+        if (head) off += es;
+        r.et = tail ? off : -1;
+        if (tail) off += es;
+        r.info = off;
+        r.pl = pl;
+        r.scr = 3 * r.lp + off + 4;
+        r.ls = r.scr + fac_scratch(g);
+        r.ih = inv_h; r.beta = beta; r.ihf = (float)inv_h; r.betaf = (float)beta;
+        r.tdiv = fac_tdiv(r.T);
+        r.c0 = c0;
+        r.own = (s0 - c0) | ((s1 - c0) << 9) | (head ? kFacOwnHead : 0) | (tail ? kFacOwnTail : 0) | kFacOwnSplit;
+        const int p0 = head ? 0 : g.first + s0 * per, p1 = tail ? pl + 1 : g.first + s1 * per;
+        const int v0 = head ? 0 : g.first + s0 * per + vsh, v1 = tail ? N + 1 : g.first + s1 * per + vsh;
+        r.sp0 = fac_ru4(p0); r.sp1 = tail ? p1 : (p1 & ~3);
+        r.sv0 = fac_ru4(v0); r.sv1 = tail ? v1 : (v1 & ~3);
+        out[i] = r;
+        const size_t sb = (fac_head_bytes(1) + (size_t)r.ls * esz + 127) & ~(size_t)127;
+        if (sb > smax) smax = sb;
+    }
+    *stage_bytes = smax;
+    return fac_stages_for(smax, esz) > 0 ? K : 0;
 }
 // Table offsets of an end region, as compile-time functions of the block size (fac_e_*).
 template <int BS>
@@ -368,7 +458,7 @@ __device__ bool fac_end(const LineDesc<TS> &d, const FacGeom &g, int end, double
 template <typename TS, int BS>
 __device__ bool fac_chunks_fp64(const LineDesc<TS> &d, const FacGeom &g, const double *dBh, const double *dBt, TS *rec) {
     constexpr int B2 = BS * BS;
-    TS *recS = rec, *recF = rec + (size_t)g.tact * B2, *recH = rec + (size_t)2 * g.tact * B2;
+    TS *recS = rec, *recF = rec + fac_part(g), *recH = rec + (size_t)2 * fac_part(g);
     auto al = [&](int k) -> double { return (double)d.alpha[(long long)k * d.sp]; };
     double G[BS][BS], Fp[BS][BS], Hp[BS][BS];
     for (int p = 0; p < BS; ++p)
@@ -477,8 +567,7 @@ __global__ void fac_precompute_kernel(const LineDesc<TS> *__restrict__ descs, in
                                   : fac_chunks_fp64<TS, 3>(d, g, dBh, dBt, rec);
     if (!ok) { atomicExch(status, 1); return; }
     const double tau = sizeof(TS) == 4 ? 0x1p-40 : 0x1p-70;
-    const int B2 = g.bs * g.bs;
-    const TS *F = rec + (size_t)g.tact * B2, *H = rec + (size_t)2 * g.tact * B2;
+    const TS *F = rec + fac_part(g), *H = rec + (size_t)2 * fac_part(g);
     const int rf = d.method == kCFD ? fac_reach<TS, 2>(F, g.tact, tau, true) : fac_reach<TS, 3>(F, g.tact, tau, true);
     const int rb = d.method == kCFD ? fac_reach<TS, 2>(H, g.tact, tau, false) : fac_reach<TS, 3>(H, g.tact, tau, false);
     TS *info = rec + fac_info(g);
@@ -697,33 +786,40 @@ __device__ void fac_store_outputs(const unsigned char *stage) {
     if (gr.T < 32) return;
     const LineDesc<T> *descs = (const LineDesc<T> *)(stage + kFacGroupBytes);
     const T *base = (const T *)(stage + fac_head_bytes(gr.nl));
-    const unsigned pbytes = round16((unsigned)(gr.pl + 1) * (unsigned)sizeof(T));
-    const unsigned vbytes = round16((unsigned)(gr.N + 1) * (unsigned)sizeof(T));
+    // stored spans [sp0, sp1) and [sv0, sv1): 4-element-aligned starts, lengths rounded up to
+    // 16 bytes only at the line's end (inside the padded line)
+    const unsigned pbytes = round16((unsigned)(gr.sp1 - gr.sp0) * (unsigned)sizeof(T));
+    const unsigned vbytes = round16((unsigned)(gr.sv1 - gr.sv0) * (unsigned)sizeof(T));
     for (int l = 0; l < gr.nl; ++l) {
-        const T *ln = base + (size_t)l * gr.ls;
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(descs[l].po),
-                     "r"(smem_addr(ln)), "r"(pbytes)
-                     : "memory");
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(descs[l].vo),
-                     "r"(smem_addr(ln + 2 * gr.lp)), "r"(vbytes)
-                     : "memory");
+        const T *sp = base + (size_t)l * gr.ls - gr.lo;  // staged element k at sp[k]
+        if (pbytes)
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(descs[l].po + gr.sp0),
+                         "r"(smem_addr(sp + gr.sp0)), "r"(pbytes)
+                         : "memory");
+        if (vbytes)
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(descs[l].vo + gr.sv0),
+                         "r"(smem_addr(sp + 2 * gr.lp + gr.sv0)), "r"(vbytes)
+                         : "memory");
     }
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // Thread 0: stage one line group (descriptors, then per line the pressure, velocity and alpha
-// lines and the record) into shared memory.  Every source line starts on a 16-byte boundary
-// (padded leading dimensions) and the copies, rounded up to 16 bytes, stay inside the padded
-// line.
-template <typename T>
+// lines and the record) into shared memory.  A sub-line of a split line stages its span of the
+// three lines and, of the record, its chunks' S, F and H parts, the end tables it holds and the
+// reach.  Every source starts on a 16-byte boundary (padded leading dimensions; spans start at
+// multiples of four elements; record parts are padded to four elements and sub-line ranges
+// start at multiples of four chunks) and the copies, rounded up to 16 bytes, stay inside the
+// padded line or the record.
+template <typename T, int BS, bool SPLIT>
 __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, const FacGroup *gp, unsigned char *stage,
                           unsigned long long *bar) {
     const FacGroup &gr = *gp;
-    const int Lp = gr.lp, R = gr.rec;
-    const unsigned bp = round16((unsigned)(gr.pl + 1) * (unsigned)sizeof(T));
-    const unsigned bv = round16((unsigned)(gr.N + 1) * (unsigned)sizeof(T));
-    const unsigned br = (unsigned)R * (unsigned)sizeof(T);
+    const int Lp = gr.lp, lo = SPLIT ? gr.lo : 0;
+    const unsigned bp = round16((unsigned)gr.pn * (unsigned)sizeof(T));
+    const unsigned bv = round16((unsigned)gr.vn * (unsigned)sizeof(T));
+    const unsigned br = (unsigned)(gr.info + 4) * (unsigned)sizeof(T);  // the staged record
     const unsigned bd = (unsigned)(gr.nl * kDescBytes);
     const unsigned bg = (unsigned)sizeof(FacGroup);
     mbar_expect_tx(bar, bg + bd + (unsigned)gr.nl * (2 * bp + bv + br));
@@ -733,10 +829,26 @@ __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, const FacGroup 
     for (int l = 0; l < gr.nl; ++l) {
         const LineDesc<T> &d = descs[gr.first + l];
         T *ln = base + (size_t)l * gr.ls;
-        bulk_to_smem(ln, d.p, bp, bar);
-        bulk_to_smem(ln + Lp, d.v, bv, bar);
-        bulk_to_smem(ln + 2 * Lp, d.alpha, bp, bar);
-        bulk_to_smem(ln + 3 * Lp, d.sep, br, bar);
+        bulk_to_smem(ln, d.p + lo, bp, bar);
+        bulk_to_smem(ln + Lp, d.v + lo, bv, bar);
+        bulk_to_smem(ln + 2 * Lp, d.alpha + lo, bp, bar);
+        if constexpr (!SPLIT) {
+            bulk_to_smem(ln + 3 * Lp, d.sep, br, bar);
+        } else {
+            const FacGeom g = fac_geom(BS == 2 ? kCFD : kMFD, gr.N);
+            const int pg = fac_part(g), es = fac_e_stride(g);
+            const size_t cs = (size_t)gr.c0 * (BS * BS);
+            const unsigned bpart = (unsigned)gr.part * (unsigned)sizeof(T);
+            const unsigned be = (unsigned)es * (unsigned)sizeof(T);
+            T *rec = ln + 3 * Lp;
+            const T *src = d.sep;
+            bulk_to_smem(rec, src + cs, bpart, bar);
+            bulk_to_smem(rec + gr.part, src + pg + cs, bpart, bar);
+            bulk_to_smem(rec + 2 * gr.part, src + 2 * pg + cs, bpart, bar);
+            if (gr.eh >= 0) bulk_to_smem(rec + gr.eh, src + 3 * pg, be, bar);
+            if (gr.et >= 0) bulk_to_smem(rec + gr.et, src + 3 * pg + es, be, bar);
+            bulk_to_smem(rec + gr.info, src + 3 * pg + 2 * es, 4u * (unsigned)sizeof(T), bar);
+        }
     }
 }
 
@@ -807,7 +919,7 @@ __device__ __forceinline__ void win_scan(bool forward, int c, int tact, int reac
 // One line group from its staged inputs: nl lines of one simulation and direction, Tl
 // threads per line; thread (l, c) = (tid / Tl, tid % Tl) owns middle blocks [c MM, c MM + MM).
 // ---------------------------------------------------------------------------------------
-template <typename T, int BS, int MM>
+template <typename T, int BS, int MM, bool SPLIT>
 __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural, int full_scan, ScanSmem<T, BS> &ssm,
                                           T *offf, T *offb) {
     static_assert(MM >= 2, "chunks of at least two blocks");
@@ -819,16 +931,25 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     const FacGroup &gr = *(const FacGroup *)stage_raw;  // staged with the lines
     const LineDesc<T> *descs = (const LineDesc<T> *)(stage_raw + kFacGroupBytes);
     T *stage = (T *)(stage_raw + fac_head_bytes(gr.nl));
-    const int N = gr.N, Tl = gr.T, tact = gr.tact;
-    const int Lp = gr.lp, R = gr.rec;
-    const int l = Tl > 1 ? (int)__umulhi((unsigned)tid, gr.tdiv) : tid, c = tid - l * Tl;
+    const int N = gr.N, Tl = gr.T, tact = gr.tact;  // tact: chunks of the group's range
+    const int Lp = gr.lp;
+    const int l = Tl > 1 ? (int)__umulhi((unsigned)tid, gr.tdiv) : tid, c = tid - l * Tl;  // c: local chunk
+    // a sub-line of a split line (SPLIT) covers the chunks c0 .. c0 + tact - 1 of its line
+    const int cg = SPLIT ? gr.c0 + c : c;  // global chunk
+    const int own = gr.own, ol0 = own & 511, ol1 = (own >> 9) & 511;
+    const bool has_head = !SPLIT || (own & kFacOwnHead) != 0, has_tail = !SPLIT || (own & kFacOwnTail) != 0;
     const bool line_ok = l < gr.nl;
     const bool act = line_ok && c < tact;
+    const bool owned = SPLIT ? act && c >= ol0 && c < ol1 : act;  // writes its outputs
+    // an owned chunk at either end of a sub-line's owned span has outputs outside the
+    // bulk-stored spans
+    const bool edge = SPLIT && (c == ol0 || c == ol1 - 1);
     const int ll = line_ok ? l : 0;
     const LineDesc<T> &d = descs[ll];
-    T *sPw = stage + (size_t)ll * gr.ls;
+    T *lb = stage + (size_t)ll * gr.ls;     // the line's staged block
+    T *sPw = SPLIT ? lb - gr.lo : lb;       // staged element k of the pressure line at sPw[k]
     const T *sP = sPw;
-    const T *sV = sP + Lp, *sA = sP + 2 * Lp, *sR = sP + 3 * Lp;
+    const T *sV = sP + Lp, *sA = sP + 2 * Lp, *sR = lb + 3 * Lp;
     const T *eH = sR + gr.eh, *eT = sR + gr.et;
     const int pl = gr.pl;
     constexpr int Z = E::Z;
@@ -840,17 +961,17 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     const int ls = c & (S - 1);           // lane index within the segment (S a power of two)
     const int sbase = lane - ls;          // first lane of the segment
     const int wl = c >> 5;                // warp index within the line (Tl >= 32)
-    const bool head_seg = Tl < 32 || wl == 0;
-    const bool tail_seg = Tl < 32 || wl == ((tact - 1) >> 5);
-    const bool is_tail = act && c == tact - 1;
+    const bool head_seg = has_head && (Tl < 32 || wl == 0);
+    const bool tail_seg = has_tail && (Tl < 32 || wl == ((tact - 1) >> 5));
+    const bool is_tail = act && has_tail && c == tact - 1;
     const int opT = pl + 1 - W, ovT = N + 1 - W;  // tail windows
 
     // ---- right-hand sides and the alpha window ----
     constexpr int NA = (BS == 2) ? MM + 2 : 3 * MM;
     T aw[NA];     // CFD: 3 alpha / h at nodes jb-1 .. jb+MM;  MFD: alpha at the chunk's cells
     T Y[MM][BS];  // r, then y, then x
-    const int jb = gr.mid + c * MM;      // CFD: first node of the chunk
-    const int cb = gr.mid + 3 * c * MM;  // MFD: first cell of the chunk
+    const int jb = gr.mid + cg * MM;      // CFD: first node of the chunk
+    const int cb = gr.mid + 3 * cg * MM;  // MFD: first cell of the chunk
     if (act) {
         if constexpr (BS == 2) {
             const T c3 = T(3) * ih;
@@ -891,13 +1012,14 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     // that at the end the end-region lanes add only the adjacent block's BS terms.
     // Row r < NR1 belongs to the head, r >= NR1 to the tail; within an end, HZ rows come first.
     constexpr int NR1 = E::HMAX + (BS == 3 ? E::HMAX + 2 : 0), NR = 2 * NR1;
-    T *scr = sPw + gr.scr;
+    T *scr = lb + gr.scr;
     // Lines of at least three warps: the warps other than the head and tail warps compute the
     // rows after their local forward pass (below), while the end warps form KZ z.
     const bool scr_help = Tl >= 96;
     if (line_ok && !scr_help) {
         auto row_win = [&](int r) {
             const bool tail = r >= NR1;
+            if (!(tail ? has_tail : has_head)) return;
             const int q = tail ? r - NR1 : r;
             const T *row = (tail ? eT : eH) + (q < E::HMAX ? E::HZ + q * Z : E::DZ + (q - E::HMAX) * Z);
             T a0 = T(0), a1 = T(0);
@@ -1088,14 +1210,15 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 const bool tail = r >= NR1;
                 const int q = tail ? r - NR1 : r;
                 T a = T(0);
-                if (r < NR) {
+                const bool here = r < NR && (tail ? has_tail : has_head);
+                if (here) {
                     const T *row = (tail ? eT : eH) + (q < E::HMAX ? E::HZ + q * Z : E::DZ + (q - E::HMAX) * Z);
                     a = row[k] * zval(tail, k);
                     if (k + 16 < 2 * W) a += row[k + 16] * zval(tail, k + 16);
                 }
 #pragma unroll
                 for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (k == 0 && r < NR) scr[r] = a;
+                if (k == 0 && here) scr[r] = a;
             }
         }
     }
@@ -1105,7 +1228,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     if (full_scan) {
         Map<T, BS> mp;
         if (act) {
-            load_blk<T, BS>(sR + tact * B2 + c * B2, mp.m);
+            load_blk<T, BS>(sR + gr.part + c * B2, mp.m);
 #pragma unroll
             for (int p = 0; p < BS; ++p) mp.off[p] = Y[MM - 1][p];
         } else {
@@ -1117,7 +1240,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
 #pragma unroll
             for (int p = 0; p < BS; ++p) lofff[c * BS + p] = Y[MM - 1][p];
         workers_sync();
-        if (act) win_scan<T, BS>(true, c, tact, (int)sinfo[0], sR + tact * B2, lofff, yin);
+        if (act) win_scan<T, BS>(true, c, tact, (int)sinfo[0], sR + gr.part, lofff, yin);
     }
     if (act) {
         T dl[BS];
@@ -1147,7 +1270,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     if (full_scan) {
         Map<T, BS> mp;
         if (act) {
-            load_blk<T, BS>(sR + 2 * tact * B2 + c * B2, mp.m);
+            load_blk<T, BS>(sR + 2 * gr.part + c * B2, mp.m);
 #pragma unroll
             for (int p = 0; p < BS; ++p) mp.off[p] = Y[0][p];
         } else {
@@ -1160,7 +1283,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
 #pragma unroll
             for (int p = 0; p < BS; ++p) loffb[c * BS + p] = Y[0][p];
         workers_sync();
-        if (act) win_scan<T, BS>(false, c, tact, (int)sinfo[1], sR + 2 * tact * B2, loffb, xin);
+        if (act) win_scan<T, BS>(false, c, tact, (int)sinfo[1], sR + 2 * gr.part, loffb, xin);
     }
     if (act) {
         T ep[BS];
@@ -1190,28 +1313,32 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     const bool stage_v = Tl >= 32;
     T *sOut = sPw + 2 * Lp;
     // source term dt/2 f(t_{m+1}) added by the thread that wrote pressure point src_k
+    // staged in shared memory inside the bulk-stored spans, stored directly outside them
+    const int sp0 = gr.sp0, sp1 = gr.sp1, sv0 = gr.sv0, sv1 = gr.sv1;
+    auto staged_p = [&](int k) { return SPLIT ? stage_v && k >= sp0 && k < sp1 : stage_v; };
+    auto staged_v = [&](int j) { return SPLIT ? stage_v && j >= sv0 && j < sv1 : stage_v; };
     auto add_source = [&]() {
         const long long m = *d.clock;
         const T s = (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(m + 1) * d.dt));
-        if (stage_v) sPw[src_k] += s; else gpo[src_k * spo] = gpo[src_k * spo] + s;
+        if (staged_p(src_k)) sPw[src_k] += s; else gpo[src_k * spo] = gpo[src_k * spo] + s;
         if (d.advance_clock) *d.clock = m + 1;
     };
     auto out_p = [&](int k, T val_out, T val_nat) {
-        if (stage_v) sPw[k] = val_out; else gpo[k * spo] = val_out;
+        if (staged_p(k)) sPw[k] = val_out; else gpo[k * spo] = val_out;
         if (uo) uo[k * snp] = val_nat;
     };
     auto out_v = [&](int j, T vin, T dv) {  // dv = beta * (D_u u*)_j
-        if (stage_v) sOut[j] = vin - T(2) * dv; else gvo[j * svo] = vin - T(2) * dv;
+        if (staged_v(j)) sOut[j] = vin - T(2) * dv; else gvo[j * svo] = vin - T(2) * dv;
         if (wo) wo[j * snv] = vin - dv;
     };
-    if (act) {
+    if (owned) {
         if constexpr (BS == 2) {
             // alpha at the chunk's nodes is aw / (3/h); p and v at the chunk's nodes
             const T inv_c3 = T(1) / (T(3) * ih);
             T wp[MM], wv[MM];
             load_win<T, MM>(sP + jb, wp);
             load_win<T, MM>(sV + jb, wv);
-            if (stage_v && !uo && !wo) {
+            if (stage_v && !uo && !wo && !edge) {
 #pragma unroll
                 for (int i = 0; i < MM; ++i) {
                     const T ae = aw[i + 1] * inv_c3 * Y[i][0];
@@ -1230,7 +1357,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
         } else {
             const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
             const T bi = beta * ih;
-            if (stage_v && !uo && !wo) {
+            if (stage_v && !uo && !wo && !edge) {
                 // staged outputs only: no per-point branches; the velocities after the last
                 // block of the tail chunk belong to the tail region
                 const T b2 = T(2) * bi;
@@ -1339,7 +1466,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
             }
         } else {
             const int cell0 = tail ? N - gr.tu + 1 : 1;
-            const int qb = gr.mid + 3 * (tact * MM - 1);
+            const int qb = gr.mid + 3 * ((cg - c + tact) * MM - 1);  // first cell of the last middle block
             const int jlo = tail ? qb + 1 : 0, nrow = tail ? N - qb : gr.hu + 2;
             if (S == 32) {
                 // one row per lane: pressure rows on lanes 0..15 (m <= HMAX), velocity rows on
@@ -1394,7 +1521,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-template <typename T, int BS, int MM>
+template <typename T, int BS, int MM, bool SPLIT>
 __global__ void __launch_bounds__(kFacThreads, 1)
 line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup *__restrict__ groups, int ngroups,
                            int natural, unsigned stage_bytes, int stages, int full_scan, int *fault) {
@@ -1427,7 +1554,7 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
                     if (!mbar_wait(&empty[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
                     fac_store_outputs<T>(stage);
                 }
-                fac_issue<T>(descs, groups + gi, stage, &full[st]);
+                fac_issue<T, BS, SPLIT>(descs, groups + gi, stage, &full[st]);
                 last[st] = use;
             }
             // the last groups of each stage: wait until solved, write their outputs
@@ -1446,7 +1573,7 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
         const int st = two ? (it & 1) : 0;
         const int use = two ? (it >> 1) : it;
         if (!mbar_wait(&full[st], (unsigned)(use & 1))) atomicExch(fault, 1);
-        fac_group<T, BS, MM>(fac_smem + (size_t)st * stage_bytes, natural, full_scan, ssm, offs[0], offs[kBufs - 1]);
+        fac_group<T, BS, MM, SPLIT>(fac_smem + (size_t)st * stage_bytes, natural, full_scan, ssm, offs[0], offs[kBufs - 1]);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
     }
@@ -1459,10 +1586,10 @@ cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, double *ws, 
     return cudaGetLastError();
 }
 
-template <typename T, int BS, int MM>
+template <typename T, int BS, int MM, bool SPLIT>
 cudaError_t launch_fac_inst(const LineDesc<T> *d, const FacGroup *groups, int ngroups, size_t stage_bytes, int stages,
                             int grid, int natural, int full_scan, int *fault, cudaStream_t s) {
-    auto kern = line_solve_factored_kernel<T, BS, MM>;
+    auto kern = line_solve_factored_kernel<T, BS, MM, SPLIT>;
     const size_t dyn = (size_t)stages * stage_bytes;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
@@ -1479,9 +1606,11 @@ cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const FacGroup *gro
     if (stages != 1 && stages != 2) return cudaErrorInvalidValue;
     const int full = max_reach > kFacMaxReach ? 1 : 0;
     switch (variant) {
-    case 0: return launch_fac_inst<T, 2, 9>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
-    case 1: return launch_fac_inst<T, 3, 2>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
-    case 2: return launch_fac_inst<T, 3, 3>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 0: return launch_fac_inst<T, 2, 9, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 1: return launch_fac_inst<T, 3, 2, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 2: return launch_fac_inst<T, 3, 3, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 3: return launch_fac_inst<T, 2, 9, true>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 4: return launch_fac_inst<T, 3, 3, true>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -63,24 +63,40 @@ size_t v1_scratch_words(int method, int N);
 
 // Factored solver (adi_factored.cu).
 // One line group of a launch, built on the host: lines [first, first + nl) of one simulation
-// and direction, with the geometry every thread of the CTA needs.
-// Copied into shared memory with the group's lines.
+// and direction, with the geometry every thread of the CTA needs; or, for a line with more
+// chunks than a CTA has threads, one sub-line: the chunks [c0, c0 + tact) of one line, of
+// which it writes the outputs of its own chunks and solves the others (a halo of at least the
+// scan reach on each interior side) only to feed its own chunks' windowed scans.
+// Copied into shared memory with the group's lines.  Offsets below are in elements.
 struct alignas(16) FacGroup {
     int first, nl, N, T;     // first descriptor, lines, cells per line, threads per line
-    int tact, hu, tu, mid;   // chunks with blocks, end-region unknowns, first middle node / cell
-    int lp, rec, eh, et;     // staged line elements, record elements, head / tail table offsets
-    int info, pl, ls, scr;   // scan-reach offset, far Dirichlet index, staged line stride, scratch offset
+    int tact, hu, tu, mid;   // chunks of the group's range, end-region unknowns, first middle node / cell
+    int lp, part, eh, et;    // staged array stride; S/F/H part of the staged record; head / tail table (-1: absent)
+    int info, pl, ls, scr;   // scan-reach offset in the staged record, far Dirichlet index, staged line stride, scratch
     double ih, beta;         // 1/h and dt/2 of the simulation
     float ihf, betaf;        // the same in FP32
     unsigned tdiv;           // ceil(2^32 / T) (0 for T = 1): thread / T = umulhi(thread, tdiv)
-    int pad1;
+    int c0;                  // global index of the range's first chunk
+    int lo, pn, vn;          // first staged line element; staged pressure/alpha and velocity elements
+    int own;                 // bits 0-8 first owned local chunk, 9-17 end of owned local chunks,
+                             // bit 18 holds the head region, bit 19 the tail region, bit 20 a split line
+    int sp0, sp1, sv0, sv1;  // pressure / velocity outputs stored by bulk copies ([sp0, sp1)); the
+                             // group's other owned outputs are stored by the threads that compute them
 };
+constexpr int kFacOwnHead = 1 << 18, kFacOwnTail = 1 << 19, kFacOwnSplit = 1 << 20;
+constexpr int kFacMaxSplit = 8;           // sub-lines of one line at most
+constexpr int kFacSplitMaxHalo = 16;      // largest scan reach a split line accepts
 FacGroup fac_group_of(int method, int N, int first, int nl, double inv_h, double beta);
+bool fac_split_line(int method, int N);  // a line of N cells needs more chunks than a CTA has threads
+// The sub-line groups of one split line (descriptor `first`) for scans of reach `halo`;
+// returns their count (0: not possible) and the largest stage among them.
+int fac_split_groups(int method, int N, int first, int halo, double inv_h, double beta, size_t esz,
+                     FacGroup *out, size_t *stage_bytes);
 bool fac_supported(int method, int N, size_t esz);  // chunks fit a CTA, stage fits smem
 size_t fac_words(int method, int N);     // elements of one line's record
 int fac_chunks(int method, int N);       // threads per line
-int fac_variant(int method, int N);      // compiled kernel instance: 0 CFD, 1-2 MFD
-constexpr int kFacVariants = 3;
+int fac_variant(int method, int N);      // compiled kernel instance: 0 CFD, 1-2 MFD, 3-4 split lines
+constexpr int kFacVariants = 5;
 int fac_lines_per_cta(int method, int N, size_t esz);
 size_t fac_stage_bytes(int method, int N, int nl, size_t esz);  // shared memory of one stage
 int fac_stages_for(size_t stage_bytes, size_t esz);  // 2 (prefetch), 1, or 0 (does not fit)
