@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-peak", action="store_true", help="skip the 8192^2 roofline leg")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--solver", default="default", choices=["default", "line", "chunked", "factored"],
                     help="line solver of the FP32 batch (default: the library's choice)")
@@ -252,20 +253,26 @@ def cpu_baseline_sample(side):
     import oracle
     from paper_2006_07583_gb300 import workloads as wl
 
+    def sample(strip, threads):
+        pts = 0
+        t0 = time.perf_counter()
+        for sp in make_specs(side, 1):
+            su, sv, sw = wl.shapes(sp.method, sp.nx, strip)
+            c = sp.c[:su[0], :su[1]].copy()
+            oracle.run(sp.method, sp.nx, strip, sp.h, sp.dt, c ** 2, np.zeros(su), np.zeros(sv),
+                       np.zeros(sw), 1, threads=threads)
+            pts += sp.nx * strip
+        return pts, time.perf_counter() - t0
+
     threads = os.cpu_count() or 1
-    strip = 256
-    pts = 0
-    t0 = time.perf_counter()
-    for sp in make_specs(side, 1):
-        su, sv, sw = wl.shapes(sp.method, sp.nx, strip)
-        c = sp.c[:su[0], :su[1]].copy()
-        oracle.run(sp.method, sp.nx, strip, sp.h, sp.dt, c ** 2, np.zeros(su), np.zeros(sv),
-                   np.zeros(sw), 1, threads=threads)
-        pts += sp.nx * strip
-    el = time.perf_counter() - t0
+    pts, el = sample(256, threads)
+    pts1, el1 = sample(32, 1)
     return {"value": pts / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "one PR step of a %dx%d strip of each of the two simulations "
-                      "(%.1f s of CPU wall time)" % (side, strip, el)}
+            "sample": "one PR step of a %dx256 strip of each of the two simulations "
+                      "(%.1f s of CPU wall time)" % (side, el),
+            "single_thread": {"value": pts1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": "one PR step of a %dx32 strip of each simulation "
+                                        "(%.1f s)" % (side, el1)}}
 
 
 def main():
@@ -345,7 +352,9 @@ def main():
             "kernel": "line_solve_factored_kernel (stage %d, CFD + MFD launches)" % dom_stage,
             "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
             "solve_ms": {"x_lines": solve_ms[1], "y_lines": solve_ms[2]},
-            "stage_ms_with_transpose": {"x_lines": avg1, "y_lines": avg2}}
+            "stage_ms_with_transpose": {"x_lines": avg1, "y_lines": avg2},
+            # the natural (u, v, w) formulation would move 7 words per point and stage
+            "frac_natural_state": achieved * 7 / 5 / peak}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -370,6 +379,8 @@ def main():
     batch.close()
     for s in sims:
         s.close()
+    if rank == 0 and not args.no_peak:
+        out["peak_8192"] = peak_leg(adi, torch, 8192, 20, peak)
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline_sample(args.side)
     if rank == 0:
@@ -377,6 +388,48 @@ def main():
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def peak_leg(adi, torch, side, steps, peak):
+    """The 8192^2 FP32 heterogeneous roofline run: one CFD and one MFD seismic simulation of
+    side^2 cells batched (split-line factored solver), `steps` graph-free half-step pairs after
+    three warm-up steps, CUDA events on the batch's stream."""
+    specs = make_specs(side, steps)
+    sims = []
+    for sp in specs:
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32)
+        s.set_source(*sp.source.as_tuple())
+        sims.append(s)
+    b = adi.Batch(sims)
+    stream = torch.cuda.Stream()
+    b.set_stream(stream.cuda_stream)
+    for _ in range(3):
+        b.half_step(1)
+        b.half_step(2)
+    stream.synchronize()
+    b.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            b.half_step(1)
+            b.half_step(2)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    solve = [b.solve_time(st) for st in (1, 2)]
+    solve_ms = max(t / max(n, 1) for t, n in solve)
+    pts = sum(sp.nx * sp.ny for sp in specs)
+    achieved = 5 * 4 * pts / (solve_ms / 1e3) / 1e9
+    solver = {0: "line", 1: "chunked", 2: "factored"}[sims[0].solver]
+    b.close()
+    for s in sims:
+        s.close()
+    return {"workload": "batched FP32 PR-ADI, 1 CFD + 1 MFD seismic sim at %dx%d cells" % (side, side),
+            "value": pts / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "solver": solver + (" (split lines)" if solver == "factored" else ""),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "solve_ms": solve_ms}}
 
 
 def e2e_leg(adi, torch, sims, batch, specs, n):
