@@ -271,6 +271,30 @@ int adi_step_static(int method, int nx, int ny, double h, double dt, int precisi
                     const void *c, const void *u, const void *v, const void *w,
                     void *u_out, void *v_out, void *w_out, void *cuda_stream);
 
+/*
+ * adi_fixed_point -- the paper's own stage solver, for comparison with the exact line solves
+ * of adi_step: nsteps Peaceman-Rachford steps (Eqs. 6-7) from time t0 in which each stage's
+ * coupled line systems (Eq. 8 / Eq. 10) are solved by the fixed-point iteration of Eq. 9
+ * (Algorithms 3-4): u_{k+1} = a - alpha (Dv v_k), v_{k+1} = v^m - beta (Du u_{k+1}), from
+ * (u_0, v_0) = (u^m, v^m) for the x-lines and (u*, w^m) for the y-lines, until the sum of the
+ * Frobenius norms of the two updates over the whole grid is at most eps or kmax sweeps have
+ * run.  The test runs on the device (no host round trip between sweeps).
+ *   method, nx, ny, h, dt, c_field, precision   as for adi_create.
+ *   u, v, w       host arrays (shapes of adi_create), read as the fields at t0 and overwritten
+ *                 with the fields at t0 + nsteps dt.
+ *   source        NULL, or 5 values (is, js, amp, f0, tdelay): a Ricker point source at U's
+ *                 point (is, js) as in adi_set_source.
+ *   kmax >= 1, eps >= 0   sweep limit and stopping threshold per stage.
+ *   sweeps        (may be NULL) receives the sweeps run over all stages of the call.
+ *   device_ms     (may be NULL) receives the device time of the steps (CUDA events; the
+ *                 host <-> device copies of the fields are outside it).
+ * Device memory (about 14 fields) is allocated for the call and freed before it returns.
+ * Errors: ADI_EINVAL (arguments), ADI_ENOMEM, ADI_ECUDA, ADI_ENOTSUP (no device).
+ */
+int adi_fixed_point(int method, int nx, int ny, double h, double dt, const double *c_field,
+                    double *u, double *v, double *w, int nsteps, double t0, const double *source,
+                    int kmax, double eps, int precision, long long *sweeps, double *device_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,9 @@ _SIGS = {
     "adi_set_solver": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_get_solver": ([_vp], ctypes.c_int),
     "adi_autotune": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp], ctypes.c_int),
+    "adi_fixed_point": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                         _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_double,
+                         ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp], ctypes.c_int),
     "adi_step": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_sync": ([_vp], ctypes.c_int),
     "adi_read_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
@@ -132,6 +135,28 @@ def step_static(method, nx, ny, h, dt, precision, c, u, v, w, u_out, v_out, w_ou
 
 def state_bytes(method, nx, ny, precision=ADI_FP32) -> int:
     return int(lib().adi_state_bytes(method, nx, ny, precision))
+
+
+def fixed_point(method, nx, ny, h, dt, c, u, v, w, nsteps, t0=0.0, source=None, kmax=6, eps=0.0,
+                precision=ADI_FP32):
+    """adi_fixed_point: nsteps PR steps with the paper's fixed-point stage solver (Eq. 9).
+    Returns (U, V, W, sweeps, device_ms); the inputs are not modified."""
+    su, sv, sw = workloads.shapes(method, nx, ny)
+    c, cp = _arr(c, su)
+    U = np.array(u, dtype=np.float64, order="C", copy=True)
+    V = np.array(v, dtype=np.float64, order="C", copy=True)
+    W = np.array(w, dtype=np.float64, order="C", copy=True)
+    for a, s in ((U, su), (V, sv), (W, sw)):
+        if a.shape != tuple(s):
+            raise ValueError("expected shape %s, got %s" % (s, a.shape))
+    src = None if source is None else np.array(source, dtype=np.float64)
+    sweeps = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().adi_fixed_point(method, nx, ny, h, dt, cp, U.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
+                                 W.ctypes.data_as(_dp), int(nsteps), float(t0),
+                                 src.ctypes.data_as(_dp) if src is not None else None, int(kmax), float(eps),
+                                 precision, ctypes.byref(sweeps), ctypes.byref(ms)), "adi_fixed_point")
+    return U, V, W, int(sweeps.value), float(ms.value)
 
 
 class Sim:
