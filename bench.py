@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-peak", action="store_true", help="skip the 8192^2 roofline leg")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's fixed-point iteration leg")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--solver", default="default", choices=["default", "line", "chunked", "factored"],
                     help="line solver of the FP32 batch (default: the library's choice)")
@@ -381,6 +382,8 @@ def main():
         s.close()
     if rank == 0 and not args.no_peak:
         out["peak_8192"] = peak_leg(adi, torch, 8192, 20, peak)
+    if rank == 0 and not args.no_paper:
+        out["paper_iteration"] = paper_leg(adi, args.side)
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline_sample(args.side)
     if rank == 0:
@@ -430,6 +433,25 @@ def peak_leg(adi, torch, side, steps, peak):
             "solver": solver + (" (split lines)" if solver == "factored" else ""),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "solve_ms": solve_ms}}
+
+
+def paper_leg(adi, side, steps=2, kmax=6):
+    """The paper's own stage solver on this GPU for comparison: the fixed-point iteration of
+    Eq. 9 with kmax sweeps per stage (no early stop), one thread per line, on the same two
+    simulations, FP32; device time of the steps."""
+    pts, ms = 0, 0.0
+    for sp in make_specs(side, steps):
+        from paper_2006_07583_gb300 import workloads as wl
+
+        su, sv, sw = wl.shapes(sp.method, sp.nx, sp.ny)
+        _, _, _, sweeps, t = adi.fixed_point(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, np.zeros(su),
+                                             np.zeros(sv), np.zeros(sw), steps, source=sp.source.as_tuple(),
+                                             kmax=kmax, eps=0.0, precision=adi.ADI_FP32)
+        pts += sp.nx * sp.ny
+        ms += t / steps
+    return {"workload": "the paper's fixed-point stage solver (Eq. 9, %d sweeps per stage, one thread "
+                        "per line), same two %dx%d simulations, FP32, one after the other" % (kmax, side, side),
+            "value": pts / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps}
 
 
 def e2e_leg(adi, torch, sims, batch, specs, n):
