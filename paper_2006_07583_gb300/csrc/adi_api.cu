@@ -29,6 +29,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <tuple>
 #include <new>
 #include <vector>
@@ -242,6 +243,10 @@ struct adi_sim {
     double h = 0, dt = 0;
     size_t esz = 4;
     DevBuf A[4], V[2], W[2], alpha, alphaT, Uo, Wo, tab, sep, cold_all, clock, status;
+    // host <-> device staging of the natural fields (FP64) and the prologue's scratch with the
+    // Thomas factors after it: allocated by the first adi_set_fields / adi_read_fields /
+    // adi_set_source after creation and kept until adi_destroy (adi_create frees its own)
+    DevBuf xfer, pro;
     int parity = 0;                           // which V/W copy is current
     int plan_base = 0;                        // parity at which the own plan was built
     std::vector<unsigned char> h_desc[2][2];  // host descriptors [parity][0 = x-lines, 1 = y-lines]
@@ -724,17 +729,30 @@ int upload_sim_descs(adi_sim *s) {
 template <typename T>
 int run_prologue_t(adi_sim *s) {
     const LineDesc<T> *cols = (const LineDesc<T> *)((unsigned char *)s->cold_all.p + s->h_desc[s->parity][0].size());
-    DevBuf tmp;
-    long long st = std::max(1, s->nlines[1]);
-    int rc = dev_alloc(tmp, (size_t)(2 * s->g.ny + 4) * st * sizeof(T));
-    if (rc) return rc;
-    cudaError_t e = launch_prologue<T>(cols, s->nlines[1], nullptr, nullptr, 0, 0, (T *)tmp.p, st, s->stream);
+    const long long st = std::max(1, s->nlines[1]);
+    const int N = s->g.ny;
+    const size_t scr = (size_t)(N + 2) * st, nfac = s->g.method == ADI_CFD ? (size_t)6 * N : 0;
+    const size_t bytes = (scr + nfac) * sizeof(T);
+    cudaError_t e = cudaSuccess;
+    if (s->pro.bytes != bytes) {  // first use: scratch plus the CFD Thomas factors of P, Pbar
+        dev_free(s->pro);
+        int rc = dev_alloc(s->pro, bytes);
+        if (rc) return rc;
+        if (nfac) {
+            std::vector<double> f;
+            prologue_factors(N, f);
+            std::vector<T> ft(f.begin(), f.end());
+            e = cudaMemcpyAsync((T *)s->pro.p + scr, ft.data(), ft.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // ft leaves scope
+        }
+    }
+    if (e == cudaSuccess)
+        e = launch_prologue<T>(cols, s->nlines[1], nfac ? (const T *)s->pro.p + scr : nullptr, (T *)s->pro.p, st, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    dev_free(tmp);
     if (e != cudaSuccess) return cuda_status(e);
     // the prologue wrote a column-major (A[3]), like a stage-2 launch
     const Geometry &g = s->g;
-    rc = transpose(s, s->A[3].p, g.ldu, g.rows_u, g.ldc, s->A[0].p, g.lda);
+    int rc = transpose(s, s->A[3].p, g.ldu, g.rows_u, g.ldc, s->A[0].p, g.lda);
     if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
     return rc;
 }
@@ -793,15 +811,24 @@ int setup_solver(adi_sim *s) {
     return rc;
 }
 
+// The FP64 staging buffer of host <-> device field copies (one field), kept once allocated.
+int xfer_buffer(adi_sim *s) {
+    const Geometry &g = s->g;
+    const size_t bytes = std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double);
+    if (s->xfer.bytes >= bytes) return ADI_OK;
+    dev_free(s->xfer);
+    return dev_alloc(s->xfer, bytes);
+}
+
 // Loads natural fields (host; NULL keeps the current natural value) into both ping-pong
 // copies and rebuilds the carried state at the current parity with the prologue (so a
 // member of a batch stays consistent with the batch's plan).
 int load_state(adi_sim *s, const double *u, const double *v, const double *w, bool keep_missing) {
     const Geometry &g = s->g;
     const size_t esz = s->esz;
-    DevBuf staging;
-    int rc = dev_alloc(staging, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
+    int rc = xfer_buffer(s);
     if (rc) return rc;
+    DevBuf &staging = s->xfer;
     const int cur = s->parity;
     if (v || !keep_missing) rc = upload(s, v, s->V[cur].p, g.rows_v, g.ldv, g.ldvp, (double *)staging.p, 1.0, 0);
     if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nVp() * esz, cudaMemcpyDeviceToDevice, s->stream));
@@ -815,22 +842,38 @@ int load_state(adi_sim *s, const double *u, const double *v, const double *w, bo
     for (int k = 1; k <= 3 && !rc; k += 2) rc = transpose(s, s->Uo.p, g.rows_u, g.ldu, g.ldu, s->A[k].p, g.ldc);
     for (int k = 0; k < 2 && !rc; ++k) rc = transpose(s, s->Wo.p, g.rows_w, g.ldw, g.ldw, s->W[k].p, g.ldwc);
     if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
-    dev_free(staging);
     if (!rc) rc = upload_sim_descs(s);  // descriptors of the current parity
     if (!rc) rc = prologue(s);
     return rc;
 }
 
-bool finite_positive(const double *x, size_t n) {
-    for (size_t i = 0; i < n; ++i)
-        if (!(std::isfinite(x[i]) && x[i] > 0.0)) return false;
+// True when ok(x[i]) holds for every i; large arrays are split over host threads.
+template <typename F>
+bool all_of_host(const double *x, size_t n, F ok) {
+    auto range = [&](size_t lo, size_t hi) {
+        bool good = true;
+        for (size_t i = lo; i < hi; ++i) good &= ok(x[i]);
+        return good;
+    };
+    const size_t kChunk = (size_t)1 << 20;
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 2 * kChunk || hw == 1) return range(0, n);
+    const unsigned nt = (unsigned)std::min<size_t>(hw, n / kChunk);
+    std::vector<std::thread> th;
+    std::vector<char> res(nt, 1);
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t] { res[t] = range(n * t / nt, n * (t + 1) / nt) ? 1 : 0; });
+    for (auto &x_ : th) x_.join();
+    for (char r : res)
+        if (!r) return false;
     return true;
+}
+bool finite_positive(const double *x, size_t n) {
+    return all_of_host(x, n, [](double v) { return std::isfinite(v) && v > 0.0; });
 }
 bool all_finite(const double *x, size_t n) {
     if (!x) return true;
-    for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(x[i])) return false;
-    return true;
+    return all_of_host(x, n, [](double v) { return std::isfinite(v); });
 }
 
 bool valid_config(int method, int nx, int ny, int precision) {
@@ -933,6 +976,8 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
     if (!rc) rc = setup_solver(s);
     if (!rc) rc = load_state(s, u0, v0, w0, false);
     if (rc) { adi_destroy(s); return rc; }
+    dev_free(s->xfer);  // set-up staging is not kept
+    dev_free(s->pro);
     *out = s;
     return ADI_OK;
 }
@@ -1102,6 +1147,7 @@ int adi_set_source(adi_handle s, int is, int js, double amp, double f0, double t
     if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
     s->plan_base = s->parity;
     if (!rc) rc = prologue(s);  // a picks up dt/2 f(t_now) at the source point
+    dev_free(s->pro);           // a one-off: the prologue's scratch is not kept
     if (rc) s->sticky = rc;
     return rc;
 }
@@ -1144,9 +1190,9 @@ int adi_read_fields(adi_handle s, double *u, double *v, double *w) {
         {s->Uo.p, u, (size_t)g.rows_u, (size_t)g.ldu, (size_t)g.ldu},
         {s->V[s->parity].p, v, (size_t)g.rows_v, (size_t)g.ldv, (size_t)g.ldvp},
         {s->Wo.p, w, (size_t)g.rows_w, (size_t)g.ldw, (size_t)g.ldw}};
-    DevBuf tmp;
-    rc = dev_alloc(tmp, std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double));
+    rc = xfer_buffer(s);
     if (rc) return rc;
+    DevBuf &tmp = s->xfer;
     for (auto &pt : parts) {
         if (!pt.dst) continue;
         const size_t n = pt.rows * pt.cols;
@@ -1159,9 +1205,8 @@ int adi_read_fields(adi_handle s, double *u, double *v, double *w) {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(pt.dst, tmp.p, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) { dev_free(tmp); return s->sticky = cuda_status(e); }
+        if (e != cudaSuccess) return s->sticky = cuda_status(e);
     }
-    dev_free(tmp);
     return ADI_OK;
 }
 
@@ -1212,7 +1257,8 @@ int adi_destroy(adi_handle s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     plan_free(s->plan);
     DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->A[2], &s->A[3], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
-                      &s->alphaT, &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status};
+                      &s->alphaT, &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status,
+                      &s->xfer, &s->pro};
     for (DevBuf *b : bufs) dev_free(*b);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     (void)cudaGetLastError();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 namespace adi {
 
@@ -51,10 +52,12 @@ cudaError_t launch_precompute(const LineDesc<T> *d, int nlines, T *tab_out_base,
 template <typename T>
 cudaError_t launch_line_solve_v1(const LineDesc<T> *d, int nlines, T *scratch,
                                  long long scratch_stride, int write_natural, cudaStream_t s);
+// fac: the Thomas factors of prologue_factors() in T, or nullptr (formed on the fly; the
+// scratch then holds two vectors per line)
 template <typename T>
-cudaError_t launch_prologue(const LineDesc<T> *col_lines, int nlines, const T *u_nat,
-                            const T *w_nat, long long u_ld, long long w_ld, T *scratch,
+cudaError_t launch_prologue(const LineDesc<T> *col_lines, int nlines, const T *fac, T *scratch,
                             long long scratch_stride, cudaStream_t s);
+void prologue_factors(int N, std::vector<double> &out);  // CFD: 3 (N+1) + 3 (N-1) values
 template <typename T>
 cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s);
 

@@ -15,6 +15,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "adi_internal.h"
 #include "adi_ops.cuh"
@@ -256,37 +257,58 @@ __global__ void __launch_bounds__(128) line_solve_v1_kernel(const LineDesc<T> *_
 //   w*_j = w_j - beta (Du u)_j                      (all velocity points)     -> d.v
 // (d.po of a stage-2 line is the stage-1 input buffer; d.v is the stage-2 input; the
 // natural u and w are read through d.u_out and d.w_out.)
-// CFD derivatives solve Pbar e = Qbar w and P g = Q u by the Thomas algorithm.
+// CFD derivatives solve Pbar e = Qbar w and P g = Q u by the Thomas algorithm, with the
+// factors of the two constant matrices precomputed (fac: P's sub-diagonal, eliminated
+// super-diagonal and inverse pivots, N+1 each, then Pbar's, N-1 each).
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__device__ void thomas_apply(int N, bool reduced, T *rhs_scr, T *c_scr, long long st) {
-    // Solves (P or Pbar) x = rhs in place; rows indexed 0..n-1 (Pbar row r is node r+1).
+__device__ void thomas_apply(int n, T *rhs, long long st, const T *__restrict__ lo, const T *__restrict__ cu,
+                             const T *__restrict__ id) {
+    // Solves the n-row system in place: forward d_r = (rhs_r - lo_r d_{r-1}) / den_r, then
+    // x_r = d_r - c_r x_{r+1}; the running value stays in a register.
+    T d = rhs[0] * id[0];
+    rhs[0] = d;
+    for (int r = 1; r < n; ++r) {
+        d = (rhs[(long long)r * st] - lo[r] * d) * id[r];
+        rhs[(long long)r * st] = d;
+    }
+    T x = d;
+    for (int r = n - 2; r >= 0; --r) {
+        x = rhs[(long long)r * st] - cu[r] * x;
+        rhs[(long long)r * st] = x;
+    }
+}
+
+// Without precomputed factors (fac == nullptr): the same elimination with each row's factors
+// formed on the fly, the eliminated super-diagonal kept in cs (stride st).
+template <typename T>
+__device__ void thomas_rows(int N, bool reduced, T *rhs, T *cs, long long st) {
     const int n = reduced ? N - 1 : N + 1;
-    auto R = [&](int k) -> T & { return rhs_scr[(long long)k * st]; };
-    auto Cp = [&](int k) -> T & { return c_scr[(long long)k * st]; };
     double w[8];
     int c0;
-    T cprev = T(0), dprev = T(0);
+    T cprev = T(0), d = T(0);
     for (int r = 0; r < n; ++r) {
-        int len = reduced ? cfd_Pbar_row(N, r + 1, &c0, w) : cfd_P_row(N, r, &c0, w);
-        int first = reduced ? c0 - 1 : c0;  // column index of the first coefficient
+        if (reduced) cfd_Pbar_row(N, r + 1, &c0, w); else cfd_P_row(N, r, &c0, w);
         T lo = T(0), di, up = T(0);
         if (r == 0) { di = (T)w[0]; up = (T)w[1]; }
         else if (r == n - 1) { lo = (T)w[0]; di = (T)w[1]; }
         else { lo = (T)w[0]; di = (T)w[1]; up = (T)w[2]; }
-        (void)first; (void)len;
-        T den = di - lo * cprev;
-        T cn = up / den;
-        T dn = (R(r) - lo * dprev) / den;
-        Cp(r) = cn; R(r) = dn;
-        cprev = cn; dprev = dn;
+        const T den = di - lo * cprev;
+        cprev = up / den;
+        d = (rhs[(long long)r * st] - lo * d) / den;
+        cs[(long long)r * st] = cprev;
+        rhs[(long long)r * st] = d;
     }
-    for (int r = n - 2; r >= 0; --r) R(r) = R(r) - Cp(r) * R(r + 1);
+    T x = d;
+    for (int r = n - 2; r >= 0; --r) {
+        x = rhs[(long long)r * st] - cs[(long long)r * st] * x;
+        rhs[(long long)r * st] = x;
+    }
 }
 
 template <typename T>
 __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nlines, T *scratch,
-                                long long st) {
+                                long long st, const T *__restrict__ fac) {
     int line = blockIdx.x * blockDim.x + threadIdx.x;
     if (line >= nlines) return;
     const LineDesc<T> d = descs[line];
@@ -312,7 +334,8 @@ __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nline
             for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
             S(j) = acc * ih;
         }
-        thomas_apply<T>(N, false, scr, scr + (long long)(N + 1) * st, st);
+        if (fac) thomas_apply<T>(N + 1, scr, st, fac, fac + (N + 1), fac + 2 * (N + 1));
+        else thomas_rows<T>(N, false, scr, scr + (long long)(N + 1) * st, st);
         for (int j = 0; j <= N; ++j) d.v[j * d.sv] = wn[j * snv] - beta * S(j);
         // e = Pbar^{-1} Qbar w  (slots 0..N-2 for nodes 1..N-1), then a = u - alpha e
         for (int j = 1; j <= N - 1; ++j) {
@@ -321,7 +344,12 @@ __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nline
             for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
             S(j - 1) = acc * ih;
         }
-        thomas_apply<T>(N, true, scr, scr + (long long)(N + 1) * st, st);
+        if (fac) {
+            const T *fb = fac + 3 * (N + 1);
+            thomas_apply<T>(N - 1, scr, st, fb, fb + (N - 1), fb + 2 * (N - 1));
+        } else {
+            thomas_rows<T>(N, true, scr, scr + (long long)(N + 1) * st, st);
+        }
         for (int j = 1; j <= N - 1; ++j) {
             T val = un[j * snp] - d.alpha[j * d.sp] * S(j - 1);
             if (j == d.src_k) val += src;
@@ -380,12 +408,38 @@ cudaError_t launch_line_solve_v1(const LineDesc<T> *d, int nlines, T *scratch, l
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_prologue(const LineDesc<T> *d, int nlines, const T *, const T *, long long,
-                            long long, T *scratch, long long st, cudaStream_t s) {
+cudaError_t launch_prologue(const LineDesc<T> *d, int nlines, const T *fac, T *scratch, long long st,
+                            cudaStream_t s) {
     if (nlines <= 0) return cudaSuccess;
     int tpb = 128;
-    prologue_kernel<T><<<(nlines + tpb - 1) / tpb, tpb, 0, s>>>(d, nlines, scratch, st);
+    prologue_kernel<T><<<(nlines + tpb - 1) / tpb, tpb, 0, s>>>(d, nlines, scratch, st, fac);
     return cudaGetLastError();
+}
+
+// Thomas factors of the App. A P (N+1 rows) and Pbar (N-1 rows), for the prologue: per matrix
+// the sub-diagonal, the eliminated super-diagonal c_r = up_r / den_r and 1 / den_r, where
+// den_r = di_r - lo_r c_{r-1}; built in FP64.
+void prologue_factors(int N, std::vector<double> &out) {
+    out.assign(3 * (N + 1) + 3 * (N - 1), 0.0);
+    for (int bar = 0; bar < 2; ++bar) {
+        const int n = bar ? N - 1 : N + 1;
+        double *lo = out.data() + (bar ? 3 * (N + 1) : 0), *cu = lo + n, *id = cu + n;
+        double cprev = 0.0;
+        for (int r = 0; r < n; ++r) {
+            double w[8];
+            int c0;
+            if (bar) cfd_Pbar_row(N, r + 1, &c0, w); else cfd_P_row(N, r, &c0, w);
+            double l = 0.0, di, up = 0.0;
+            if (r == 0) { di = w[0]; up = w[1]; }
+            else if (r == n - 1) { l = w[0]; di = w[1]; }
+            else { l = w[0]; di = w[1]; up = w[2]; }
+            const double den = di - l * cprev;
+            lo[r] = l;
+            cu[r] = up / den;
+            id[r] = 1.0 / den;
+            cprev = cu[r];
+        }
+    }
 }
 template <typename T>
 cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s) {
@@ -401,8 +455,7 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
                                               cudaStream_t);                                 \
     template cudaError_t launch_line_solve_v1<T>(const LineDesc<T> *, int, T *, long long,   \
                                                  int, cudaStream_t);                         \
-    template cudaError_t launch_prologue<T>(const LineDesc<T> *, int, const T *, const T *,  \
-                                            long long, long long, T *, long long,            \
+    template cudaError_t launch_prologue<T>(const LineDesc<T> *, int, const T *, T *, long long,  \
                                             cudaStream_t);                                   \
     template cudaError_t launch_finite_check<T>(const T *, size_t, int *, cudaStream_t);
 ADI_INST(float)

@@ -202,7 +202,7 @@ int step_static(int method, int nx, int ny, double h, double dt, const T *c, con
     if (e == cudaSuccess) e = cudaMemcpyAsync(w_out, w, g.nW * esz, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = launch_precompute<T>(dd, nl, tab, status, s);
     // carried state a, w* from the natural fields (read through the y-lines' u_out/w_out)
-    if (e == cudaSuccess) e = launch_prologue<T>(dd + g.piy, g.pix, nullptr, nullptr, 0, 0, scr, L.st, s);
+    if (e == cudaSuccess) e = launch_prologue<T>(dd + g.piy, g.pix, nullptr, scr, L.st, s);
     if (e == cudaSuccess) e = launch_line_solve_v1<T>(dd, g.piy, scr, L.st, 0, s);
     if (e == cudaSuccess) e = launch_line_solve_v1<T>(dd + g.piy, g.pix, scr, L.st, 1, s);
     int singular = 0;
