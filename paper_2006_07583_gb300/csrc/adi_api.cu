@@ -731,7 +731,7 @@ int run_prologue_t(adi_sim *s) {
     const LineDesc<T> *cols = (const LineDesc<T> *)((unsigned char *)s->cold_all.p + s->h_desc[s->parity][0].size());
     const long long st = std::max(1, s->nlines[1]);
     const int N = s->g.ny;
-    const size_t scr = (size_t)(N + 2) * st, nfac = s->g.method == ADI_CFD ? (size_t)6 * N : 0;
+    const size_t scr = (size_t)(2 * N + 2) * st, nfac = s->g.method == ADI_CFD ? (size_t)6 * N : 0;
     const size_t bytes = (scr + nfac) * sizeof(T);
     cudaError_t e = cudaSuccess;
     if (s->pro.bytes != bytes) {  // first use: scratch plus the CFD Thomas factors of P, Pbar
@@ -747,7 +747,8 @@ int run_prologue_t(adi_sim *s) {
         }
     }
     if (e == cudaSuccess)
-        e = launch_prologue<T>(cols, s->nlines[1], nfac ? (const T *)s->pro.p + scr : nullptr, (T *)s->pro.p, st, s->stream);
+        e = launch_prologue_lines<T>(cols, s->nlines[1], N, s->g.method, nfac ? (const T *)s->pro.p + scr : nullptr,
+                                     (T *)s->pro.p, st, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_status(e);
     // the prologue wrote a column-major (A[3]), like a stage-2 launch

@@ -58,6 +58,12 @@ template <typename T>
 cudaError_t launch_prologue(const LineDesc<T> *col_lines, int nlines, const T *fac, T *scratch,
                             long long scratch_stride, cudaStream_t s);
 void prologue_factors(int N, std::vector<double> &out);  // CFD: 3 (N+1) + 3 (N-1) values
+// The prologue over the y-lines of one simulation (N cells each) with one thread per line
+// element for the stencils (and, for CFD, one per line for the Thomas solves with fac).
+// scratch: 2N elements per line (element k at k * st + line).
+template <typename T>
+cudaError_t launch_prologue_lines(const LineDesc<T> *col_lines, int nlines, int N, int method, const T *fac,
+                                  T *scratch, long long st, cudaStream_t s);
 template <typename T>
 cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s);
 

@@ -378,6 +378,122 @@ __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nline
 }
 
 // ---------------------------------------------------------------------------------------
+// The same prologue with one thread per (line, element) for everything but the CFD Thomas
+// solves.  prologue_stencil_kernel: block (32 lines, 8 elements); for CFD it leaves
+// (Q u)_j / h (j = 0..N) and (Qbar w)_j / h (j = 1..N-1) in the scratch (element k of a line
+// at k * st + line), for MFD it writes w* and a directly.  prologue_solve_kernel (CFD, one
+// thread per line): the two Thomas solves with the precomputed factors, each output written
+// as its back-substitution produces it.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T prologue_src(const LineDesc<T> &d) {
+    return (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(*d.clock) * d.dt));
+}
+
+template <typename T>
+__global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, int nlines, int N, int method,
+                                        T *scratch, long long st) {
+    const int line = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    if (line >= nlines || j > N + 1) return;
+    const LineDesc<T> &d = descs[line];
+    const T ih = (T)d.inv_h, beta = (T)d.beta;
+    const T *un = d.u_out, *wn = d.w_out;
+    const long long snp = d.snp, snv = d.snv;
+    double w[8];
+    int c0;
+    if (method == kCFD) {
+        if (j <= N) {
+            const int n = cfd_Q_row(N, j, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+            scratch[(long long)j * st + line] = acc * ih;
+        }
+        if (j >= 1 && j <= N - 1) {
+            const int n = cfd_Qbar_row(N, j, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+            scratch[(long long)(N + j) * st + line] = acc * ih;
+        }
+    } else {
+        if (j <= N) {
+            const int n = mfd_G_row(N, j, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+            d.v[j * d.sv] = wn[j * snv] - beta * acc * ih;
+        }
+        if (j >= 1 && j <= N) {
+            const int n = mfd_D_row(N, j - 1, &c0, w);
+            T acc = T(0);
+            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+            T val = un[j * snp] - d.alpha[j * d.sp] * acc * ih;
+            if (j == d.src_k) val += prologue_src(d);
+            d.po[j * d.spo] = val;
+        } else {
+            d.po[(long long)j * d.spo] = un[(long long)j * snp];  // j = 0 or N+1: Dirichlet
+        }
+    }
+}
+
+template <typename T>
+__global__ void prologue_solve_kernel(const LineDesc<T> *__restrict__ descs, int nlines, int N, const T *scratch,
+                                      long long st, const T *__restrict__ fac) {
+    const int line = blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const LineDesc<T> &d = descs[line];
+    const T beta = (T)d.beta;
+    const T *un = d.u_out, *wn = d.w_out;
+    const long long snp = d.snp, snv = d.snv, spo = d.spo;
+    T *q = (T *)scratch + line;
+    // P g = (Q u)/h over rows 0..N; w*_j = w_j - beta g_j
+    {
+        const T *lo = fac, *cu = fac + (N + 1), *id = fac + 2 * (N + 1);
+        T dd = q[0] * id[0];
+        q[0] = dd;
+#pragma unroll 4
+        for (int r = 1; r <= N; ++r) {
+            dd = (q[(long long)r * st] - lo[r] * dd) * id[r];
+            q[(long long)r * st] = dd;
+        }
+        T x = dd;
+        d.v[(long long)N * d.sv] = wn[(long long)N * snv] - beta * x;
+#pragma unroll 4
+        for (int r = N - 1; r >= 0; --r) {
+            x = q[(long long)r * st] - cu[r] * x;
+            d.v[(long long)r * d.sv] = wn[(long long)r * snv] - beta * x;
+        }
+    }
+    // Pbar e = (Qbar w)/h over nodes 1..N-1 (rows 0..N-2); a_j = u_j - alpha_j e_j (+ source)
+    {
+        const T *fb = fac + 3 * (N + 1);
+        const T *lo = fb, *cu = fb + (N - 1), *id = fb + 2 * (N - 1);
+        T *qb = q + (long long)(N + 1) * st;  // element r = node r + 1
+        T dd = qb[0] * id[0];
+        qb[0] = dd;
+#pragma unroll 4
+        for (int r = 1; r < N - 1; ++r) {
+            dd = (qb[(long long)r * st] - lo[r] * dd) * id[r];
+            qb[(long long)r * st] = dd;
+        }
+        const T src = d.src_k >= 0 ? prologue_src(d) : T(0);
+        T x = dd;
+        auto out = [&](int r, T e) {
+            const int j = r + 1;
+            T val = un[(long long)j * snp] - d.alpha[(long long)j * d.sp] * e;
+            if (j == d.src_k) val += src;
+            d.po[(long long)j * spo] = val;
+        };
+        out(N - 2, x);
+#pragma unroll 4
+        for (int r = N - 3; r >= 0; --r) {
+            x = qb[(long long)r * st] - cu[r] * x;
+            out(r, x);
+        }
+        d.po[0] = un[0];
+        d.po[(long long)N * spo] = un[(long long)N * snp];
+    }
+}
+
 template <typename T>
 __global__ void finite_check_kernel(const T *__restrict__ x, size_t n, int *flag) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -413,6 +529,17 @@ cudaError_t launch_prologue(const LineDesc<T> *d, int nlines, const T *fac, T *s
     if (nlines <= 0) return cudaSuccess;
     int tpb = 128;
     prologue_kernel<T><<<(nlines + tpb - 1) / tpb, tpb, 0, s>>>(d, nlines, scratch, st, fac);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prologue_lines(const LineDesc<T> *d, int nlines, int N, int method, const T *fac, T *scratch,
+                                  long long st, cudaStream_t s) {
+    if (nlines <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((nlines + 31) / 32), (unsigned)((N + 2 + 7) / 8));
+    prologue_stencil_kernel<T><<<grid, dim3(32, 8), 0, s>>>(d, nlines, N, method, scratch, st);
+    if (method == kCFD)
+        prologue_solve_kernel<T><<<(nlines + 127) / 128, 128, 0, s>>>(d, nlines, N, scratch, st, fac);
     return cudaGetLastError();
 }
 
@@ -456,7 +583,9 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
     template cudaError_t launch_line_solve_v1<T>(const LineDesc<T> *, int, T *, long long,   \
                                                  int, cudaStream_t);                         \
     template cudaError_t launch_prologue<T>(const LineDesc<T> *, int, const T *, T *, long long,  \
-                                            cudaStream_t);                                   \
+                                            cudaStream_t);                                         \
+    template cudaError_t launch_prologue_lines<T>(const LineDesc<T> *, int, int, int, const T *, T *, \
+                                                  long long, cudaStream_t);                                   \
     template cudaError_t launch_finite_check<T>(const T *, size_t, int *, cudaStream_t);
 ADI_INST(float)
 ADI_INST(double)
