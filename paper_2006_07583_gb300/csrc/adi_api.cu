@@ -821,6 +821,27 @@ int xfer_buffer(adi_sim *s) {
     return dev_alloc(s->xfer, bytes);
 }
 
+// Finite check of host fields on the device, before any of the simulation's state changes:
+// each field is copied into the staging buffer and scanned there (ADI_EINVAL on NaN/Inf).
+int check_finite_on_device(adi_sim *s, const double *u, const double *v, const double *w) {
+    int rc = xfer_buffer(s);
+    if (rc) return rc;
+    const Geometry &g = s->g;
+    const double *f[3] = {u, v, w};
+    const size_t n[3] = {g.nU(), g.nV(), g.nW()};
+    cudaError_t e = cudaMemsetAsync(s->status.p, 0, sizeof(int), s->stream);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        if (!f[k]) continue;
+        e = cudaMemcpyAsync(s->xfer.p, f[k], n[k] * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = launch_finite_check<double>((const double *)s->xfer.p, n[k], (int *)s->status.p, s->stream);
+    }
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, s->status.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return flag ? ADI_EINVAL : ADI_OK;
+}
+
 // Loads natural fields (host; NULL keeps the current natural value) into both ping-pong
 // copies and rebuilds the carried state at the current parity with the prologue (so a
 // member of a batch stays consistent with the batch's plan).
@@ -1219,8 +1240,9 @@ int adi_set_fields(adi_handle s, const double *u, const double *v, const double 
     }
     int rc = adi_sync(s);
     if (rc) return rc;
-    const Geometry &g = s->g;
-    if (!all_finite(u, g.nU()) || !all_finite(v, g.nV()) || !all_finite(w, g.nW())) return ADI_EINVAL;
+    rc = check_finite_on_device(s, u, v, w);
+    if (rc == ADI_EINVAL) return rc;
+    if (rc) return s->sticky = rc;
     rc = load_state(s, u, v, w, true);
     if (rc) s->sticky = rc;
     return rc;

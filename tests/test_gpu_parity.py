@@ -292,3 +292,23 @@ def test_split_lines_vs_oracle(adi, method, precision):
             assert _max_rel(g, o) <= 1e-12
         else:
             assert _l2_rel(g, o) <= 1e-4
+
+
+def test_set_fields_rejects_nonfinite_and_keeps_state(adi):
+    """adi_set_fields checks its host inputs on the device before touching the state: a NaN
+    or Inf in any field gives ADI_EINVAL and the fields read exactly as before."""
+    method, nx, ny = CFD, 40, 30
+    h, dt, c, U, V, W = _random_case(method, nx, ny, seed=91)
+    s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=adi.ADI_FP32)
+    s.step(3)
+    before = s.read()
+    for k, bad in ((0, np.nan), (1, np.inf), (2, -np.inf)):
+        fields = [f.copy() for f in before]
+        fields[k][3, 4] = bad
+        with pytest.raises(adi.AdiError) as e:
+            s.set_fields(*fields)
+        assert e.value.code == 1  # ADI_EINVAL
+        for a, b in zip(s.read(), before):
+            assert np.array_equal(a, b)
+    s.set_fields(*before)  # finite inputs are accepted
+    s.close()
