@@ -122,9 +122,13 @@ extern "C" {
 size_t adi_server_bytes(int method, int nx, int ny, int precision) {
     const size_t st = adi_state_bytes(method, nx, ny, precision);
     if (!st) return 0;
-    const size_t lines = method == ADI_CFD ? (size_t)(nx - 1) + (ny - 1) : (size_t)nx + ny;
+    const size_t xl = method == ADI_CFD ? (size_t)(ny - 1) : (size_t)ny;  // x-lines (nx cells each)
+    const size_t yl = method == ADI_CFD ? (size_t)(nx - 1) : (size_t)nx;  // y-lines (ny cells each)
+    // groups per line: one at most, or up to kFacMaxSplit sub-lines for a split line
+    const size_t gx = adi::fac_split_line(method, nx) ? adi::kFacMaxSplit : 1;
+    const size_t gy = adi::fac_split_line(method, ny) ? adi::kFacMaxSplit : 1;
     // the batch's own descriptor copies (two parities) and line-group table
-    return st + 2 * lines * sizeof(adi::LineDesc<double>) + lines * sizeof(adi::FacGroup);
+    return st + 2 * (xl + yl) * sizeof(adi::LineDesc<double>) + (xl * gx + yl * gy) * sizeof(adi::FacGroup);
 }
 
 int adi_server_create(adi_server *out, size_t hbm_budget, int precision, int quantum, int max_active) {
