@@ -468,6 +468,12 @@ def e2e_leg(adi, torch, sims, batch, specs, n):
     batch.sync()
     for s, bb in zip(sims, bufs):
         s.read_into(*bb)
+    for s, bb in zip(sims, bufs):  # one untimed round trip: first-use buffers are set up here
+        s.set_fields(*bb)
+    batch.step(1)
+    batch.sync()
+    for s, bb in zip(sims, bufs):
+        s.read_into(*bb)
     t0 = time.perf_counter()
     for _ in range(n):
         for s, bb in zip(sims, bufs):
