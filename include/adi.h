@@ -158,7 +158,8 @@ int adi_check_finite(adi_handle sim);
 /* Completed steps and the simulation time t = steps * dt. */
 int adi_get_time(adi_handle sim, long long *steps, double *t);
 
-/* adi_destroy -- frees everything the handle owns (NULL is accepted). */
+/* adi_destroy -- frees everything the handle owns (NULL is accepted); ADI_EBUSY, freeing
+ * nothing, while the handle is a member of a batch or of an unfinished ticket. */
 int adi_destroy(adi_handle sim);
 
 /*
@@ -270,6 +271,26 @@ int adi_server_destroy(adi_server s);
 int adi_step_static(int method, int nx, int ny, double h, double dt, int precision,
                     const void *c, const void *u, const void *v, const void *w,
                     void *u_out, void *v_out, void *w_out, void *cuda_stream);
+
+/*
+ * adi_batch_submit -- runs simulations with their own step counts as one asynchronous batch
+ * and returns at once with a ticket.  Every member with steps left advances together (one
+ * persistent, graph-launched plan per phase over all their lines); a member whose count is
+ * reached leaves and the others go on.  Until adi_batch_poll reports the ticket done, the
+ * members are busy: adi_step, adi_set_solver, adi_set_source, adi_autotune, adi_batch_create,
+ * adi_batch_submit and adi_destroy return ADI_EBUSY; adi_read_fields and adi_set_fields wait
+ * for the ticket's work first.
+ *   sims[n], nsteps[n]   distinct handles of one precision, none in a batch or ticket;
+ *                        nsteps[k] >= 0.
+ * Errors: ADI_EINVAL, ADI_EBUSY, ADI_ENOMEM, ADI_ECUDA (nothing is run then).
+ *
+ * adi_batch_poll -- *done = 1 once every step of the ticket has finished (the members are
+ * released and the ticket retired), else 0; never blocks.  The poll that retires a ticket
+ * returns the run's error, if any (also made sticky on its members).  ADI_EINVAL for an
+ * unknown or retired ticket.
+ */
+int adi_batch_submit(const adi_handle *sims, const int *nsteps, int n, int *ticket);
+int adi_batch_poll(int ticket, int *done);
 
 /*
  * adi_fixed_point -- the paper's own stage solver, for comparison with the exact line solves

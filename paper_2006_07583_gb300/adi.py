@@ -53,6 +53,9 @@ _SIGS = {
     "adi_set_solver": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_get_solver": ([_vp], ctypes.c_int),
     "adi_autotune": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp], ctypes.c_int),
+    "adi_batch_submit": ([ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                          ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "adi_batch_poll": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "adi_fixed_point": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp,
                          _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_double,
                          ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp], ctypes.c_int),
@@ -135,6 +138,24 @@ def step_static(method, nx, ny, h, dt, precision, c, u, v, w, u_out, v_out, w_ou
 
 def state_bytes(method, nx, ny, precision=ADI_FP32) -> int:
     return int(lib().adi_state_bytes(method, nx, ny, precision))
+
+
+def batch_submit(sims, nsteps):
+    """adi_batch_submit: advance each simulation by its own step count as one asynchronous
+    batch; returns the ticket (poll it with batch_poll)."""
+    n = len(sims)
+    hs = (_vp * n)(*[s.handle for s in sims])
+    st = (ctypes.c_int * n)(*[int(k) for k in nsteps])
+    t = ctypes.c_int(0)
+    _check(lib().adi_batch_submit(hs, st, n, ctypes.byref(t)), "adi_batch_submit")
+    return t.value
+
+
+def batch_poll(ticket):
+    """adi_batch_poll: True once the ticket's steps have all finished (never blocks)."""
+    d = ctypes.c_int(0)
+    _check(lib().adi_batch_poll(int(ticket), ctypes.byref(d)), "adi_batch_poll")
+    return bool(d.value)
 
 
 def fixed_point(method, nx, ny, h, dt, c, u, v, w, nsteps, t0=0.0, source=None, kmax=6, eps=0.0,
@@ -241,8 +262,8 @@ class Sim:
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
-            _lib.adi_destroy(self._h)
-            self._h = None
+            if _lib.adi_destroy(self._h) != 6:  # ADI_EBUSY: still in a batch; keep the handle
+                self._h = None
 
     def __del__(self):
         try:

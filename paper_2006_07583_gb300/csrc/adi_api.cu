@@ -1277,6 +1277,7 @@ int adi_get_time(adi_handle s, long long *steps, double *t) {
 
 int adi_destroy(adi_handle s) {
     if (!s) return ADI_OK;
+    if (s->in_batch) return ADI_EBUSY;  // a batch or ticket still refers to it
     if (s->stream) cudaStreamSynchronize(s->stream);
     plan_free(s->plan);
     DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->A[2], &s->A[3], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
@@ -1403,6 +1404,124 @@ int adi_batch_solve_time(adi_batch b, int stage, double *total_ms, int *count) {
     if (count) *count = (int)(used / 2);
     used = 0;
     return ADI_OK;
+}
+
+// ----------------------------------------------------------------------------------------
+// Asynchronous batches with per-simulation step counts (adi_batch_submit / adi_batch_poll).
+// ----------------------------------------------------------------------------------------
+namespace {
+
+struct Ticket {
+    std::vector<adi_sim *> sims;
+    std::vector<Plan *> plans;  // one per phase, kept until the ticket completes
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+std::mutex g_ticket_mu;
+std::map<int, Ticket *> g_tickets;
+int g_next_ticket = 1;
+
+void ticket_free(Ticket *t) {
+    if (t->stream) cudaStreamSynchronize(t->stream);
+    for (Plan *p : t->plans) { plan_free(*p); delete p; }
+    for (adi_sim *s : t->sims) { s->in_batch = false; s->batch_stream = nullptr; }
+    if (t->done) cudaEventDestroy(t->done);
+    if (t->stream) cudaStreamDestroy(t->stream);
+    (void)cudaGetLastError();
+    delete t;
+}
+
+}  // namespace
+
+int adi_batch_submit(const adi_handle *sims, const int *nsteps, int n, int *ticket) {
+    if (!sims || !nsteps || n < 1 || !ticket) return ADI_EINVAL;
+    const int prec = sims[0] ? sims[0]->precision : -1;
+    for (int k = 0; k < n; ++k) {
+        if (!sims[k] || nsteps[k] < 0 || sims[k]->precision != prec) return ADI_EINVAL;
+        if (sims[k]->in_batch) return ADI_EBUSY;
+        if (sims[k]->sticky) return sims[k]->sticky;
+        for (int q = 0; q < k; ++q)
+            if (sims[q] == sims[k]) return ADI_EINVAL;
+    }
+    Ticket *t = new (std::nothrow) Ticket;
+    if (!t) return ADI_ENOMEM;
+    cudaStream_t up = nullptr;
+    int rc = cuda_status(cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking));
+    if (!rc) rc = cuda_status(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking));
+    if (!rc) rc = cuda_status(cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming));
+    std::vector<int> par0(n);
+    for (int k = 0; k < n && !rc; ++k) {
+        rc = cuda_status(cudaStreamSynchronize(sims[k]->stream));
+        t->sims.push_back(sims[k]);
+        par0[k] = sims[k]->parity;
+    }
+    // Phases: every member with steps left advances together until the smallest remaining
+    // count is reached; the members done by then leave.  Each phase's plan is built (on a
+    // separate stream, so that nothing waits for the earlier phases' kernels) with every
+    // member at the parity it will have when the phase starts.
+    int done_steps = 0;
+    while (!rc) {
+        std::vector<adi_sim *> active;
+        int next = 0;
+        for (int k = 0; k < n; ++k)
+            if (nsteps[k] > done_steps) {
+                active.push_back(sims[k]);
+                if (next == 0 || nsteps[k] < next) next = nsteps[k];
+            }
+        if (active.empty()) break;
+        for (int k = 0; k < n; ++k) sims[k]->parity = par0[k] ^ (done_steps & 1);
+        Plan *p = new (std::nothrow) Plan;
+        if (!p) { rc = ADI_ENOMEM; break; }
+        t->plans.push_back(p);
+        rc = plan_build(*p, active, up);
+        const int run = next - done_steps;
+        if (!rc) rc = cuda_status(run == 1 ? enqueue_steps(*p, 0, 1, t->stream) : run_graph(*p, 0, run, t->stream));
+        done_steps = next;
+    }
+    for (int k = 0; k < n; ++k) sims[k]->parity = par0[k];
+    if (up) cudaStreamDestroy(up);
+    if (!rc) rc = cuda_status(cudaEventRecord(t->done, t->stream));
+    if (rc) {
+        ticket_free(t);
+        return rc;
+    }
+    for (int k = 0; k < n; ++k) {
+        sims[k]->parity = par0[k] ^ (nsteps[k] & 1);
+        sims[k]->steps += nsteps[k];
+        sims[k]->in_batch = true;
+        sims[k]->batch_stream = t->stream;
+    }
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    *ticket = g_next_ticket++;
+    g_tickets[*ticket] = t;
+    return ADI_OK;
+}
+
+int adi_batch_poll(int ticket, int *done) {
+    if (!done) return ADI_EINVAL;
+    *done = 0;
+    Ticket *t = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ticket_mu);
+        auto it = g_tickets.find(ticket);
+        if (it == g_tickets.end()) return ADI_EINVAL;
+        t = it->second;
+    }
+    const cudaError_t q = cudaEventQuery(t->done);
+    if (q == cudaErrorNotReady) return ADI_OK;
+    int rc = cuda_status(q);
+    for (Plan *p : t->plans)
+        if (!rc) rc = plan_fault(*p, t->stream);
+    {
+        std::lock_guard<std::mutex> lk(g_ticket_mu);
+        g_tickets.erase(ticket);
+    }
+    std::vector<adi_sim *> sims = t->sims;
+    ticket_free(t);
+    if (rc)
+        for (adi_sim *s : sims) s->sticky = rc;
+    *done = 1;
+    return rc;
 }
 
 int adi_batch_destroy(adi_batch b) {
