@@ -18,8 +18,9 @@
  *            (ny+2) x (nx+1) (x-nodes), W is (ny+1) x (nx+2) (y-nodes); U's corners are
  *            unused.
  *     The wave speed c is given where U lives; density is 1 and kappa = c^2.
- *   - Dirichlet data: the pressure values on U's outer rows and columns at creation are
- *     held fixed for the whole run (time-independent walls; zero for a free surface).
+ *   - Dirichlet data: the pressure values on U's outer rows and columns (as given to
+ *     adi_create or adi_set_fields) are held fixed while stepping (time-independent walls;
+ *     zero for a free surface).
  *   - nx, ny >= 16 (ADI_MIN_CELLS) and <= ADI_MAX_CELLS.
  *   - Every function returns an adi_status (0 = ADI_OK).  Errors from device work are
  *     sticky per handle: once a kernel fails, later calls on that handle return the same
@@ -82,8 +83,9 @@ const char *adi_strerror(int code);
  *   precision  ADI_FP32 (bulk arithmetic FP32, per-line factors precomputed in FP64) or
  *              ADI_FP64.
  * The simulation clock starts at t = 0.  On failure *out is NULL.
- * Device memory: about (4 fields + 2 output fields) x points x sizeof(real) plus the line
- * scratch; adi_state_bytes() reports the exact figure.
+ * Device memory: the carried state in both line layouts, two velocity copies each, alpha
+ * in both layouts, the natural outputs and the solver's per-line records (about 15 fields'
+ * worth at 4096^2 in FP32); adi_state_bytes() reports the exact figure.
  */
 int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
                const double *c_field, const double *u0, const double *v0, const double *w0,
@@ -91,8 +93,11 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
 
 /*
  * adi_set_solver -- choose the line solver of a handle (adi_solver); rebuilds its per-line
- * factors.  ADI_ENOTSUP if the chunked solver cannot take lines this long; ADI_EBUSY inside
- * a batch.  adi_get_solver returns the current one (-1 for a NULL handle).
+ * factors.  ADI_ENOTSUP if the requested solver cannot take lines this long; ADI_EBUSY
+ * inside a batch.  Lines longer than one CTA's chunks run as split lines in the factored
+ * solver; where a split line's scan reach exceeds what a sub-line's halo takes, the handle
+ * falls back to the chunked solver.  adi_get_solver returns the current one (-1 for a NULL
+ * handle).
  */
 int adi_set_solver(adi_handle sim, int solver);
 int adi_get_solver(adi_handle sim);
