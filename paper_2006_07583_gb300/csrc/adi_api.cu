@@ -1459,6 +1459,8 @@ int adi_batch_submit(const adi_handle *sims, const int *nsteps, int n, int *tick
     // count is reached; the members done by then leave.  Each phase's plan is built (on a
     // separate stream, so that nothing waits for the earlier phases' kernels) with every
     // member at the parity it will have when the phase starts.
+    // All plans first: a failure here leaves every member untouched.
+    std::vector<int> runs;
     int done_steps = 0;
     while (!rc) {
         std::vector<adi_sim *> active;
@@ -1474,15 +1476,24 @@ int adi_batch_submit(const adi_handle *sims, const int *nsteps, int n, int *tick
         if (!p) { rc = ADI_ENOMEM; break; }
         t->plans.push_back(p);
         rc = plan_build(*p, active, up);
-        const int run = next - done_steps;
-        if (!rc) rc = cuda_status(run == 1 ? enqueue_steps(*p, 0, 1, t->stream) : run_graph(*p, 0, run, t->stream));
+        runs.push_back(next - done_steps);
         done_steps = next;
     }
     for (int k = 0; k < n; ++k) sims[k]->parity = par0[k];
     if (up) cudaStreamDestroy(up);
-    if (!rc) rc = cuda_status(cudaEventRecord(t->done, t->stream));
     if (rc) {
         ticket_free(t);
+        return rc;
+    }
+    for (size_t i = 0; i < t->plans.size() && !rc; ++i) {
+        const int run = runs[i];
+        rc = cuda_status(run == 1 ? enqueue_steps(*t->plans[i], 0, 1, t->stream)
+                                  : run_graph(*t->plans[i], 0, run, t->stream));
+    }
+    if (!rc) rc = cuda_status(cudaEventRecord(t->done, t->stream));
+    if (rc) {  // some phases may have run: the members' state is no longer known
+        ticket_free(t);
+        for (int k = 0; k < n; ++k) sims[k]->sticky = rc;
         return rc;
     }
     for (int k = 0; k < n; ++k) {
