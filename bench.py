@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-peak", action="store_true", help="skip the 8192^2 roofline leg")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper's fixed-point iteration leg")
+    ap.add_argument("--ref-budget", type=float, default=REF_BUDGET_S,
+                    help="seconds of oracle work the reference arm aims at")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--solver", default="default", choices=["default", "line", "chunked", "factored"],
                     help="line solver of the FP32 batch (default: the library's choice)")
@@ -223,8 +225,8 @@ def run_reference(args):
     t0 = time.perf_counter()
     one(cases_for(16))
     per_row = (time.perf_counter() - t0) / 16
-    strip = int(REF_BUDGET_S / max(1, args.steps + args.warmup) / max(per_row, 1e-9))
-    strip = max(16, min(512, strip))
+    strip = int(args.ref_budget / max(1, args.steps + args.warmup) / max(per_row, 1e-9))
+    strip = max(16, min(512, args.side, strip))
     cases = cases_for(strip)
     pts = sum(nx * ny for _, nx, ny, *_ in cases)
     for _ in range(args.warmup):
