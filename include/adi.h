@@ -321,6 +321,16 @@ int adi_fixed_point(int method, int nx, int ny, double h, double dt, const doubl
                     double *u, double *v, double *w, int nsteps, double t0, const double *source,
                     int kmax, double eps, int precision, long long *sweeps, double *device_ms);
 
+/*
+ * adi_selftest_wait_timeout -- runs the failure path of the kernels' bounded waits on
+ * purpose: one GPU thread waits on an mbarrier that nothing arrives at, polling at most
+ * `polls` times (1 .. 2^22; the line kernels use 2^22), then gives up as a line kernel does
+ * when its staged inputs never land.  *gave_up = 1 when the wait ran out (the expected
+ * result), 0 if it completed; *cycles (may be NULL) the SM clock cycles it took.  The kernel
+ * always ends; nothing else waits on it.  Errors: ADI_EINVAL, ADI_ECUDA, ADI_ENOTSUP.
+ */
+int adi_selftest_wait_timeout(int polls, int *gave_up, long long *cycles);
+
 #ifdef __cplusplus
 }
 #endif

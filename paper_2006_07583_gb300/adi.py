@@ -53,6 +53,8 @@ _SIGS = {
     "adi_set_solver": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_get_solver": ([_vp], ctypes.c_int),
     "adi_autotune": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp], ctypes.c_int),
+    "adi_selftest_wait_timeout": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)],
+                                  ctypes.c_int),
     "adi_batch_submit": ([ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                           ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "adi_batch_poll": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -138,6 +140,14 @@ def step_static(method, nx, ny, h, dt, precision, c, u, v, w, u_out, v_out, w_ou
 
 def state_bytes(method, nx, ny, precision=ADI_FP32) -> int:
     return int(lib().adi_state_bytes(method, nx, ny, precision))
+
+
+def selftest_wait_timeout(polls):
+    """adi_selftest_wait_timeout: (gave_up, cycles) of a bounded wait that nothing completes."""
+    g = ctypes.c_int(0)
+    c = ctypes.c_longlong(0)
+    _check(lib().adi_selftest_wait_timeout(int(polls), ctypes.byref(g), ctypes.byref(c)), "adi_selftest_wait_timeout")
+    return bool(g.value), int(c.value)
 
 
 def batch_submit(sims, nsteps):

@@ -36,6 +36,7 @@
 
 #include <algorithm>
 
+#include "../../include/adi.h"
 #include "adi_internal.h"
 #include "adi_line.cuh"
 #include "adi_ops.cuh"
@@ -768,8 +769,8 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
 }
 // Waits for the phase with the given parity; gives up after a bounded number of polls
 // (each poll may suspend the thread for a short hardware-defined time).
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-    for (int i = 0; i < (1 << 22); ++i)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int polls = 1 << 22) {
+    for (int i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -1622,4 +1623,38 @@ template cudaError_t launch_line_solve_factored<float>(const LineDesc<float> *, 
 template cudaError_t launch_line_solve_factored<double>(const LineDesc<double> *, const FacGroup *, int, int, size_t,
                                                         int, int, int, int, int *, cudaStream_t);
 
+// The bounded wait's failure path, run on purpose: one thread waits on an mbarrier that
+// nothing arrives at, with `polls` polls at most, and records whether the wait gave up (and
+// the time it took).  No other thread or copy is involved, so the kernel always ends.
+__global__ void wait_timeout_probe_kernel(int polls, int *gave_up, long long *cycles) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    const long long t0 = clock64();
+    const bool ok = mbar_wait(&bar, 0u, polls);
+    *cycles = clock64() - t0;
+    *gave_up = ok ? 0 : 1;
+}
+
 }  // namespace adi
+
+extern "C" int adi_selftest_wait_timeout(int polls, int *gave_up, long long *cycles) {
+    if (polls < 1 || polls > (1 << 22) || !gave_up) return ADI_EINVAL;
+    int *d_flag = nullptr;
+    long long *d_cyc = nullptr;
+    cudaError_t e = cudaMalloc(&d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_cyc, sizeof(long long));
+    if (e == cudaSuccess) {
+        adi::wait_timeout_probe_kernel<<<1, 32>>>(polls, d_flag, d_cyc);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(gave_up, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    long long c = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&c, d_cyc, sizeof(long long), cudaMemcpyDeviceToHost);
+    if (cycles) *cycles = c;
+    if (d_flag) cudaFree(d_flag);
+    if (d_cyc) cudaFree(d_cyc);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return e == cudaErrorNoDevice ? ADI_ENOTSUP : ADI_ECUDA; }
+    return ADI_OK;
+}
