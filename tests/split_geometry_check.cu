@@ -90,6 +90,29 @@ int main() {
                     for (int k = 0; k <= pl; ++k) CHECK(pown[k] == 1, "p %d owned %d", k, pown[k]);
                     for (int k = 0; k <= N; ++k) CHECK(vown[k] == 1, "v %d owned %d", k, vown[k]);
                 }
+    // every line length: a supported line fits the CTA (threads, shared memory) as a whole
+    // line or as sub-lines, and its end regions fit their tables
+    for (int method = 0; method < 2; ++method)
+        for (int N = ADI_MIN_CELLS; N <= ADI_MAX_CELLS; N += (N < 600 ? 1 : 37))
+            for (size_t esz : {(size_t)4, (size_t)8}) {
+                if (!fac_supported(method, N, esz)) continue;
+                const FacGeom g = fac_geom(method, N);
+                CHECK(g.hu <= g.hmax && g.tu <= g.hmax && g.tact >= 1, "ends N %d", N);
+                CHECK(g.nb == g.tact * g.mm, "blocks N %d", N);
+                if (!fac_split_line(method, N)) {
+                    const int nl = fac_lines_per_cta(method, N, esz);
+                    CHECK(nl >= 1 && nl * g.T <= kFacMaxT, "lines per CTA N %d", N);
+                    const size_t sb = fac_stage_bytes(method, N, nl, esz);
+                    CHECK(fac_stages_for(sb, esz) >= 1, "stage N %d", N);
+                    CHECK((size_t)fac_stages_for(sb, esz) * sb + fac_static_smem(esz) <= kFacSmemLimit, "smem N %d", N);
+                } else {
+                    FacGroup sub[kFacMaxSplit];
+                    size_t sb = 0;
+                    const int K = fac_split_groups(method, N, 0, kFacSplitMaxHalo, 1.0, 1.0, esz, sub, &sb);
+                    CHECK(K >= 2, "split N %d", N);
+                    CHECK((size_t)fac_stages_for(sb, esz) * sb + fac_static_smem(esz) <= kFacSmemLimit, "split smem N %d", N);
+                }
+            }
     printf("bad %d\n", bad);
     return bad != 0;
 }
