@@ -66,3 +66,21 @@ def test_host_only_helpers(libpath):
     b32 = L.adi_state_bytes(0, 64, 64, 0)
     b64 = L.adi_state_bytes(0, 64, 64, 1)
     assert 0 < b32 < b64
+
+
+def test_without_a_device_the_path_fails_loudly(libpath):
+    """No CPU fallback: with no CUDA device every compute entry point returns ADI_ENOTSUP."""
+    import numpy as np
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2006_07583_gb300 import adi, workloads as wl
+
+    su, sv, sw = wl.shapes(0, 32, 32)
+    with pytest.raises(adi.AdiError) as e:
+        adi.Sim(0, 32, 32, 1.0 / 32, 0.01, np.ones(su))
+    assert e.value.code == 7
+    with pytest.raises(adi.AdiError) as e:
+        adi.fixed_point(0, 32, 32, 1.0 / 32, 0.01, np.ones(su), np.zeros(su), np.zeros(sv), np.zeros(sw), 1)
+    assert e.value.code == 7
