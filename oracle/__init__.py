@@ -63,7 +63,7 @@ def _load():
         lib.oracle_run.argtypes = [
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
             dp, dp, dp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int, ctypes.c_double,
-            ctypes.c_int,
+            ctypes.c_int, ctypes.POINTER(ctypes.c_int),
         ]
         lib.oracle_run.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
@@ -113,11 +113,13 @@ def line_solve(method, N, h, alpha, beta, a, vm, ub0=0.0, ub1=0.0, dense=False):
 
 
 def run(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0=0.0, source=None, kmax=0,
-        eps=0.0, threads=1):
+        eps=0.0, threads=1, return_sweeps=False):
     """Advances copies of (U, V, W) by ``nsteps`` PR steps; returns the new (U, V, W).
 
     source: None or (is, js, amp, f0, tdelay), a Ricker point source f = s(t)/h^2 at U[is, js].
     kmax: 0 = exact line solves; > 0 = the paper's fixed-point iteration (Eq. 9).
+    return_sweeps: also return an (nsteps, 2) int array with the sweeps each stage took in
+    the fixed-point mode (zeros for exact solves).
     """
     su, sv, sw = field_shapes(method, nx, ny)
     kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -128,11 +130,15 @@ def run(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0=0.0, source=None, kmax
     src = None
     if source is not None:
         src = np.array(source, dtype=np.float64)
+    sweeps = np.zeros((max(int(nsteps), 1), 2), dtype=np.int32)
     rc = _load().oracle_run(method, nx, ny, h, dt, _ptr(kappa), _ptr(U), _ptr(V), _ptr(W),
                             int(nsteps), float(t0), _ptr(src) if src is not None else None,
-                            int(kmax), float(eps), int(threads))
+                            int(kmax), float(eps), int(threads),
+                            sweeps.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if rc:
         raise RuntimeError("oracle_run failed: %d" % rc)
+    if return_sweeps:
+        return U, V, W, sweeps[:int(nsteps)].copy()
     return U, V, W
 
 

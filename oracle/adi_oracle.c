@@ -535,7 +535,7 @@ static double frob_diff(const double *a, const double *b, size_t n) {
  * Algorithms 3/4) with at most kmax sweeps and stopping threshold eps on the sum of the
  * Frobenius norms of the updates. */
 static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double *W,
-                   double t, const src_t *src, int kmax, double eps, int nthreads) {
+                   double t, const src_t *src, int kmax, double eps, int nthreads, int *sweeps) {
     const int nx = g->nx, ny = g->ny;
     const int ldu = g->ldu, ldv = g->ldv, ldw = g->ldw;
     const int pix = n_int(g, nx), piy = n_int(g, ny); /* interior pressure counts */
@@ -613,6 +613,7 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
             ++k;
             if (test <= eps || k >= kmax) break;
         }
+        if (sweeps) sweeps[0] = k;
         free(Uk); free(Vk);
     }
 
@@ -693,6 +694,7 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
             ++k;
             if (test <= eps || k >= kmax) break;
         }
+        if (sweeps) sweeps[1] = k;
         free(Uk); free(Wk);
     }
 
@@ -711,10 +713,12 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
  * src: NULL, or {is, js, amp, f0, tdelay} for a Ricker point source at U[is][js].
  * kmax: 0 for exact line solves, > 0 for the paper's fixed-point iteration.
  * nthreads: OpenMP threads over grid lines (1 = sequential).
+ * sweeps: NULL, or 2 * nsteps ints that receive, per step, the fixed-point sweeps that
+ * stage 1 and stage 2 took (kmax > 0 only; left untouched for exact solves).
  * Returns 0, -1 for invalid arguments, -2 for a singular line system. */
 int oracle_run(int method, int nx, int ny, double h, double dt, const double *kappa,
                double *U, double *V, double *W, int nsteps, double t0, const double *src,
-               int kmax, double eps, int nthreads) {
+               int kmax, double eps, int nthreads, int *sweeps) {
     if ((method != OR_CFD && method != OR_MFD) || nx < 8 || ny < 8 || !(h > 0.0) ||
         !(dt > 0.0) || nsteps < 0 || kmax < 0)
         return -1;
@@ -729,7 +733,9 @@ int oracle_run(int method, int nx, int ny, double h, double dt, const double *ka
     }
     int rc = 0;
     for (int m = 0; m < nsteps && rc == 0; ++m)
-        if (pr_step(&g, kappa, U, V, W, t0 + m * dt, &s, kmax, eps, nthreads)) rc = -2;
+        if (pr_step(&g, kappa, U, V, W, t0 + m * dt, &s, kmax, eps, nthreads,
+                    sweeps ? sweeps + 2 * m : NULL))
+            rc = -2;
     grid_free(&g);
     return rc;
 }
