@@ -66,6 +66,12 @@ def _load():
             ctypes.c_int, ctypes.POINTER(ctypes.c_int),
         ]
         lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_run_harmonic.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+            dp, dp, dp, ctypes.c_int, ctypes.c_double, dp, dp, dp, ctypes.c_double,
+            ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+        ]
+        lib.oracle_run_harmonic.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -139,6 +145,35 @@ def run(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0=0.0, source=None, kmax
         raise RuntimeError("oracle_run failed: %d" % rc)
     if return_sweeps:
         return U, V, W, sweeps[:int(nsteps)].copy()
+    return U, V, W
+
+
+def run_harmonic(method, nx, ny, h, dt, kappa, U, V, W, nsteps, B, F=None, omega=1.0,
+                 phase_b=0.0, phase_f=0.0, t0=0.0, source=None, kmax=0, eps=0.0, threads=1):
+    """run() with time-harmonic Dirichlet data u = B cos(omega t + phase_b) on U's walls and
+    forcing f = F cos(omega t + phase_f) at the interior pressure points (Eq. 11's problem).
+    U must hold the walls at t0."""
+    su, sv, sw = field_shapes(method, nx, ny)
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    V = np.array(V, dtype=np.float64, order="C", copy=True)
+    W = np.array(W, dtype=np.float64, order="C", copy=True)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    assert kappa.shape == su and U.shape == su and V.shape == sv and W.shape == sw
+    assert B.shape == su
+    Fp = None
+    if F is not None:
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        assert F.shape == su
+        Fp = _ptr(F)
+    src = None if source is None else np.array(source, dtype=np.float64)
+    rc = _load().oracle_run_harmonic(method, nx, ny, h, dt, _ptr(kappa), _ptr(U), _ptr(V),
+                                     _ptr(W), int(nsteps), float(t0),
+                                     _ptr(src) if src is not None else None, _ptr(B), Fp,
+                                     float(omega), float(phase_b), float(phase_f), int(kmax),
+                                     float(eps), int(threads))
+    if rc:
+        raise RuntimeError("oracle_run_harmonic failed: %d" % rc)
     return U, V, W
 
 

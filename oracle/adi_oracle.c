@@ -28,7 +28,9 @@
  *   - explicit y/x derivatives of pressure act on the whole line including its boundary
  *     values (Alg. 1/2 print reduced index sets there);
  *   - rho = 1, kappa = c^2, so alpha = dt/2 * kappa and beta = dt/2;
- *   - Dirichlet data are time independent; the intermediate u* keeps them.
+ *   - Dirichlet data are time independent (u* keeps them), except in the time-harmonic
+ *     mode of the manufactured problem (Eq. 11), where u* on the x-line ends takes the
+ *     wall value at the half step t_m + dt/2.
  *
  * Array layouts (row-major, i = y index, j = x index):
  *   CFD: U, V, W, kappa are (ny+1) x (nx+1) nodal arrays.
@@ -491,6 +493,33 @@ static double ricker(const src_t *s, double t) {
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Time-harmonic Dirichlet data and distributed forcing (the manufactured problem of      */
+/* Sec. 4, Eq. 11): u = B cos(omega t + phb) on the outer rows/columns of U, and           */
+/* f = F cos(omega t + phf) at the interior pressure points.                              */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct { const double *B, *F; double omega, phb, phf; } harm_t;
+
+static double harm_b(const harm_t *hb, size_t p, double t) {
+    return hb->B[p] * cos(hb->omega * t + hb->phb);
+}
+
+/* Writes B cos(omega t + phb) into the given edges of a U-shaped array: rows 0 and
+ * rows_u - 1 (south/north) and/or columns 0 and ldu - 1 (west/east). */
+static void harm_edges(const harm_t *hb, double *U, int rows_u, int ldu, double t, int sn, int we) {
+    if (sn)
+        for (int j = 0; j < ldu; ++j) {
+            U[j] = harm_b(hb, (size_t)j, t);
+            U[(size_t)(rows_u - 1) * ldu + j] = harm_b(hb, (size_t)(rows_u - 1) * ldu + j, t);
+        }
+    if (we)
+        for (int i = 0; i < rows_u; ++i) {
+            U[(size_t)i * ldu] = harm_b(hb, (size_t)i * ldu, t);
+            U[(size_t)i * ldu + ldu - 1] = harm_b(hb, (size_t)i * ldu + ldu - 1, t);
+        }
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* One Peaceman-Rachford step on the whole grid (Eqs. 6-7 with Eq. 8 / Eq. 10).           */
 /* ------------------------------------------------------------------------------------ */
 
@@ -535,7 +564,8 @@ static double frob_diff(const double *a, const double *b, size_t n) {
  * Algorithms 3/4) with at most kmax sweeps and stopping threshold eps on the sum of the
  * Frobenius norms of the updates. */
 static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double *W,
-                   double t, const src_t *src, int kmax, double eps, int nthreads, int *sweeps) {
+                   double t, const src_t *src, const harm_t *hb, int kmax, double eps,
+                   int nthreads, int *sweeps) {
     const int nx = g->nx, ny = g->ny;
     const int ldu = g->ldu, ldv = g->ldv, ldw = g->ldw;
     const int pix = n_int(g, nx), piy = n_int(g, ny); /* interior pressure counts */
@@ -571,6 +601,16 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
         free(ucol); free(wcol); free(dg); free(de);
     }
     if (src->on) A[(size_t)src->is * ldu + src->js] += 0.5 * dt * ricker(src, t) / (g->h * g->h);
+    if (hb && hb->F) {
+        const double ft = cos(hb->omega * t + hb->phf);
+        for (int i = 1; i <= piy; ++i)
+            for (int j = 1; j <= pix; ++j) {
+                size_t p = (size_t)i * ldu + j;
+                A[p] += 0.5 * dt * hb->F[p] * ft;
+            }
+    }
+    /* the intermediate u* at the ends of the x-lines (west/east walls): u0(t + dt/2) */
+    if (hb) harm_edges(hb, Us, g->rows_u, ldu, t + 0.5 * dt, 0, 1);
 
     /* ---- stage 1 implicit x-lines: (ubar*, v*) ---- */
     if (kmax == 0) {
@@ -580,8 +620,8 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
             double *ub = (double *)malloc(sizeof(double) * pix);
             for (int k = 0; k < pix; ++k) al[k] = 0.5 * dt * kappa[(size_t)i * ldu + k + 1];
             int rc = line_solve(&g->ox, &g->lx, al, beta, &A[(size_t)i * ldu + 1],
-                                &V[(size_t)i * ldv], U[(size_t)i * ldu],
-                                U[(size_t)i * ldu + g->ox.nu - 1], ub, &Vs[(size_t)i * ldv]);
+                                &V[(size_t)i * ldv], Us[(size_t)i * ldu],
+                                Us[(size_t)i * ldu + g->ox.nu - 1], ub, &Vs[(size_t)i * ldv]);
             if (rc) fail = 1;
             for (int k = 0; k < pix; ++k) Us[(size_t)i * ldu + k + 1] = ub[k];
             free(al); free(ub);
@@ -636,12 +676,22 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
     }
     if (src->on)
         A[(size_t)src->is * ldu + src->js] += 0.5 * dt * ricker(src, t + dt) / (g->h * g->h);
+    if (hb && hb->F) {
+        const double ft = cos(hb->omega * (t + dt) + hb->phf);
+        for (int i = 1; i <= piy; ++i)
+            for (int j = 1; j <= pix; ++j) {
+                size_t p = (size_t)i * ldu + j;
+                A[p] += 0.5 * dt * hb->F[p] * ft;
+            }
+    }
 
     /* ---- stage 2 implicit y-lines: (ubar^{m+1}, w^{m+1}) ---- */
     double *Wn = (double *)malloc(sizeof(double) * nW);
     memcpy(Wn, Ws, sizeof(double) * nW);
     double *Un = (double *)malloc(sizeof(double) * nU);
     memcpy(Un, Us, sizeof(double) * nU);
+    /* the ends of the y-lines (south/north walls) at the new time level */
+    if (hb) harm_edges(hb, Un, g->rows_u, ldu, t + dt, 1, 0);
     if (kmax == 0) {
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
         for (int j = 1; j <= pix; ++j) {
@@ -656,8 +706,8 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
                 cc[k] = A[p];
             }
             for (int r = 0; r < g->oy.nv; ++r) wv[r] = Ws[(size_t)r * ldw + j];
-            int rc = line_solve(&g->oy, &g->ly, al, beta, cc, wv, U[j],
-                                U[(size_t)(g->oy.nu - 1) * ldu + j], ub, wo);
+            int rc = line_solve(&g->oy, &g->ly, al, beta, cc, wv, Un[j],
+                                Un[(size_t)(g->oy.nu - 1) * ldu + j], ub, wo);
             if (rc) fail = 1;
             for (int k = 0; k < piy; ++k) Un[(size_t)(k + 1) * ldu + j] = ub[k];
             for (int r = 0; r < g->oy.nv; ++r) Wn[(size_t)r * ldw + j] = wo[r];
@@ -698,6 +748,8 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
         free(Uk); free(Wk);
     }
 
+    /* every wall at the new time level */
+    if (hb) harm_edges(hb, Un, g->rows_u, ldu, t + dt, 1, 1);
     memcpy(U, Un, sizeof(double) * nU);
     memcpy(V, Vn, sizeof(double) * nV);
     memcpy(W, Wn, sizeof(double) * nW);
@@ -716,9 +768,9 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
  * sweeps: NULL, or 2 * nsteps ints that receive, per step, the fixed-point sweeps that
  * stage 1 and stage 2 took (kmax > 0 only; left untouched for exact solves).
  * Returns 0, -1 for invalid arguments, -2 for a singular line system. */
-int oracle_run(int method, int nx, int ny, double h, double dt, const double *kappa,
-               double *U, double *V, double *W, int nsteps, double t0, const double *src,
-               int kmax, double eps, int nthreads, int *sweeps) {
+static int run_all(int method, int nx, int ny, double h, double dt, const double *kappa,
+                   double *U, double *V, double *W, int nsteps, double t0, const double *src,
+                   const harm_t *hb, int kmax, double eps, int nthreads, int *sweeps) {
     if ((method != OR_CFD && method != OR_MFD) || nx < 8 || ny < 8 || !(h > 0.0) ||
         !(dt > 0.0) || nsteps < 0 || kmax < 0)
         return -1;
@@ -733,11 +785,35 @@ int oracle_run(int method, int nx, int ny, double h, double dt, const double *ka
     }
     int rc = 0;
     for (int m = 0; m < nsteps && rc == 0; ++m)
-        if (pr_step(&g, kappa, U, V, W, t0 + m * dt, &s, kmax, eps, nthreads,
+        if (pr_step(&g, kappa, U, V, W, t0 + m * dt, &s, hb, kmax, eps, nthreads,
                     sweeps ? sweeps + 2 * m : NULL))
             rc = -2;
     grid_free(&g);
     return rc;
+}
+
+int oracle_run(int method, int nx, int ny, double h, double dt, const double *kappa,
+               double *U, double *V, double *W, int nsteps, double t0, const double *src,
+               int kmax, double eps, int nthreads, int *sweeps) {
+    return run_all(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0, src, NULL, kmax, eps,
+                   nthreads, sweeps);
+}
+
+/* oracle_run with time-harmonic Dirichlet data and forcing (Sec. 4, Eq. 11):
+ *   B      U-shaped; u = B cos(omega t + phb) on U's outer rows and columns.  The caller's
+ *          U must already hold the walls at t0.
+ *   F      U-shaped or NULL; f = F cos(omega t + phf) at the interior pressure points, added
+ *          as Eqs. 6-7 add the source (dt/2 f(t_m) in stage 1, dt/2 f(t_{m+1}) in stage 2).
+ * The intermediate u* at the x-line ends (west and east walls) is u0(t_m + dt/2); the
+ * y-line ends (south and north walls) take u0(t_{m+1}). */
+int oracle_run_harmonic(int method, int nx, int ny, double h, double dt, const double *kappa,
+                        double *U, double *V, double *W, int nsteps, double t0,
+                        const double *src, const double *B, const double *F, double omega,
+                        double phb, double phf, int kmax, double eps, int nthreads) {
+    if (!B) return -1;
+    harm_t hb = {B, F, omega, phb, phf};
+    return run_all(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0, src, &hb, kmax, eps,
+                   nthreads, NULL);
 }
 
 int oracle_num_threads(void) {

@@ -76,6 +76,59 @@ def standing_wave(method: int, n: int, t: float):
     return U, V, W
 
 
+@dataclass
+class HarmonicProblem:
+    """The exact solution of Sec. 4, Eq. 11 on the unit square (c = 1, rho = 1):
+
+        u = Psi(x, y) cos(omega t),  Psi = Gamma (x^k - (1-x)^k + y^k - (1-y)^k)
+                                          + sin(2 pi x / lam) sin(2 pi y / lam),
+
+    omega = 2 pi / T, with the velocities that the momentum equation of Eq. 1 gives from
+    v = w = 0 at t = 0, (v, w) = -(1/omega) grad Psi sin(omega t), and the forcing that makes
+    the pressure equation exact, f = -sin(omega t) (omega Psi + (kappa/omega) Laplacian Psi).
+    In the time-harmonic form of the ADI engine: walls u = B cos(omega t + phase_b) with
+    B = Psi, forcing f = F cos(omega t + phase_f) with F = omega Psi + Laplacian Psi / omega
+    and phase_f = pi/2."""
+    method: int
+    n: int
+    gamma: float
+    k: int
+    lam: float
+    period: float
+
+    @property
+    def omega(self) -> float:
+        return 2.0 * math.pi / self.period
+
+    def _psi(self, x, y):
+        g, k, a = self.gamma, self.k, 2.0 * math.pi / self.lam
+        X, Y = np.meshgrid(x, y)
+        psi = g * (X ** k - (1 - X) ** k + Y ** k - (1 - Y) ** k) + np.sin(a * X) * np.sin(a * Y)
+        px = g * k * (X ** (k - 1) + (1 - X) ** (k - 1)) + a * np.cos(a * X) * np.sin(a * Y)
+        py = g * k * (Y ** (k - 1) + (1 - Y) ** (k - 1)) + a * np.sin(a * X) * np.cos(a * Y)
+        lap = (g * k * (k - 1) * (X ** (k - 2) - (1 - X) ** (k - 2) + Y ** (k - 2) - (1 - Y) ** (k - 2))
+               - 2.0 * a * a * np.sin(a * X) * np.sin(a * Y))
+        return psi, px, py, lap
+
+    def fields(self, t: float):
+        """Exact (U, V, W) at time t."""
+        h = 1.0 / self.n
+        (ux, uy), (vx, vy), (wx, wy) = point_coords(self.method, self.n, self.n, h)
+        om = self.omega
+        U = self._psi(ux, uy)[0] * math.cos(om * t)
+        V = -self._psi(vx, vy)[1] * math.sin(om * t) / om
+        W = -self._psi(wx, wy)[2] * math.sin(om * t) / om
+        return U, V, W
+
+    def amplitudes(self):
+        """(B, F, omega, phase_b, phase_f) for the engine's and the oracle's harmonic mode."""
+        h = 1.0 / self.n
+        (ux, uy), _, _ = point_coords(self.method, self.n, self.n, h)
+        psi, _, _, lap = self._psi(ux, uy)
+        om = self.omega
+        return psi, om * psi + lap / om, om, 0.0, 0.5 * math.pi
+
+
 def unit_kappa(method: int, nx: int, ny: int) -> np.ndarray:
     return np.ones(shapes(method, nx, ny)[0], dtype=np.float64)
 
