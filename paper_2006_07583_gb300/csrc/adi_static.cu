@@ -35,7 +35,9 @@ int status_of(cudaError_t e) {
 }
 
 // Address of the scratch array on the current device; the first call for a device looks it
-// up with that device current.
+// up with that device current and keeps it for the life of the process (a cudaDeviceReset,
+// or a driver context other than the device's primary one, would make the kept address
+// stale: the entry point is for processes that keep one primary context per device).
 int scratch_on_current_device(unsigned char **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -212,6 +214,25 @@ int step_static(int method, int nx, int ny, double h, double dt, const T *c, con
     return singular ? ADI_ESINGULAR : ADI_OK;
 }
 
+// Every pointer must be device (or managed) memory of the current device: host memory
+// handed here by mistake would fault the caller's context in the first copy or kernel, so it
+// is refused before anything is enqueued.  cudaPointerGetAttributes allocates nothing.
+int check_device_pointers(const void *const ins[4], const void *const outs[3]) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { (void)cudaGetLastError(); return status_of(e); }
+    const void *all[7] = {ins[0], ins[1], ins[2], ins[3], outs[0], outs[1], outs[2]};
+    for (const void *p : all) {
+        cudaPointerAttributes a;
+        std::memset(&a, 0, sizeof(a));
+        e = cudaPointerGetAttributes(&a, p);
+        if (e != cudaSuccess) { (void)cudaGetLastError(); return ADI_EINVAL; }
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return ADI_EINVAL;
+        if (a.device != dev) return ADI_EINVAL;
+    }
+    return ADI_OK;
+}
+
 }  // namespace
 
 extern "C" int adi_step_static(int method, int nx, int ny, double h, double dt, int precision,
@@ -231,6 +252,10 @@ extern "C" int adi_step_static(int method, int nx, int ny, double h, double dt, 
             if (outs[o] == outs[k]) return ADI_EINVAL;
     }
     if (nx > ADI_STATIC_MAX_CELLS || ny > ADI_STATIC_MAX_CELLS) return ADI_ENOMEM;
+    {
+        const int rc = check_device_pointers(ins, outs);
+        if (rc) return rc;
+    }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (precision == ADI_FP64)
         return step_static<double>(method, nx, ny, h, dt, (const double *)c, (const double *)u,

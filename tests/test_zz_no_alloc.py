@@ -2,9 +2,20 @@
 device array of the library) against the handle path (adi_create + adi_step + adi_read_fields
 with the thread-per-line solver) on the same seeded inputs, over two calls in a row.
 
-Both paths launch the same kernels in the same order on the same values, so they agree to
-rounding; the tolerance is the path's FP64 / FP32 parity bound.
+Some callers cannot allocate device memory: a process whose device memory is wholly taken by
+its own pool, or a latency-bound loop that cannot take the device-wide synchronisation of
+cudaFree.  This entry point serves them, so the test also checks that the calls leave the
+device's free memory and torch's allocation count unchanged.
+
+The line solves are the same kernels on the same values in both paths; the carried state
+before them comes from different prologue kernels (the handle path's per-element stencils
+with FP64-built Thomas factors, the static path's one-thread-per-line prologue that forms the
+factors in the working precision), so the results agree to a few rounding units: 1e-12 (FP64)
+and 2e-6 (FP32) of the largest value.  A wrong carried-state, boundary or output copy would
+show up at order one.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -40,23 +51,36 @@ def _case(method, nx, ny, seed, dtype):
     return h, dt, c, U, V, W
 
 
+# the largest layouts (CFD 128 x 128 in FP64 is the biggest user of the array) and rectangles
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("method,nx,ny", [(CFD, 40, 29), (MFD, 33, 47), (MFD, 128, 128)])
+@pytest.mark.parametrize("method,nx,ny", [(CFD, 40, 29), (MFD, 33, 47), (MFD, 128, 128),
+                                          (CFD, 128, 128), (MFD, 128, 17), (CFD, 17, 128)])
 def test_static_step_matches_handle_path_twice(env, method, nx, ny, prec):
     adi, torch = env
     precision = adi.ADI_FP64 if prec == "fp64" else adi.ADI_FP32
     np_t = np.float64 if prec == "fp64" else np.float32
     t_t = torch.float64 if prec == "fp64" else torch.float32
-    tol = 1e-12 if prec == "fp64" else 1e-5
+    tol = 1e-12 if prec == "fp64" else 2e-6
     h, dt, c, U, V, W = _case(method, nx, ny, 11 + nx, np_t)
 
     sim = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=precision, solver=adi.ADI_SOLVER_LINE)
     dev = [torch.tensor(a.astype(np_t), dtype=t_t, device="cuda") for a in (c, U, V, W)]
     out = [torch.empty_like(x) for x in dev[1:]]
+    nxt = [torch.empty_like(x) for x in dev[1:]]
+    # one untimed call first (the array's address is looked up on the device's first call)
+    adi.step_static(method, nx, ny, h, dt, precision, *[x.data_ptr() for x in dev],
+                    *[x.data_ptr() for x in nxt])
     torch.cuda.synchronize()
     for call in range(2):
+        # objects of earlier tests may still be collected and free device memory; an
+        # allocation by the call could only lower the free figure
+        gc.collect()
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         adi.step_static(method, nx, ny, h, dt, precision, *[x.data_ptr() for x in dev],
                         *[x.data_ptr() for x in out])
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] >= free0 and torch.cuda.memory_allocated() == alloc0
         sim.step(1)
         Uh, Vh, Wh = sim.read()
         for got, ref, name in zip(out, (Uh, Vh, Wh), "uvw"):
@@ -64,7 +88,8 @@ def test_static_step_matches_handle_path_twice(env, method, nx, ny, prec):
             err = np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-300)
             assert err <= tol, (call, name, err)
         # the outputs become the next call's inputs
-        dev = [dev[0]] + [x.clone() for x in out]
+        for d, o in zip(dev[1:], out):
+            d.copy_(o)
     sim.close()
 
 
@@ -82,3 +107,23 @@ def test_static_step_rejects_sizes_beyond_capacity(env):
         adi.step_static(CFD, 32, 32, 1.0 / 32, 0.5 / 32, adi.ADI_FP64, *[x.data_ptr() for x in b[:4]],
                         b[1].data_ptr(), b[5].data_ptr(), b[6].data_ptr())
     assert ex.value.code == 1  # ADI_EINVAL
+
+
+def test_static_step_rejects_host_pointers(env):
+    """Host memory handed as a field is refused before any work is enqueued (ADI_EINVAL), and
+    the device stays usable."""
+    adi, torch = env
+    nx = ny = 32
+    su, sv, sw = wl.shapes(CFD, nx, ny)
+    dev = [torch.zeros(s, dtype=torch.float64, device="cuda") for s in (su, su, sv, sw, su, sv, sw)]
+    dev[0] += 1.0
+    host = np.ones(su)
+    ptrs = [x.data_ptr() for x in dev]
+    for k in range(7):
+        bad = list(ptrs)
+        bad[k] = host.ctypes.data
+        with pytest.raises(adi.AdiError) as ex:
+            adi.step_static(CFD, nx, ny, 1.0 / nx, 0.5 / nx, adi.ADI_FP64, *bad)
+        assert ex.value.code == 1  # ADI_EINVAL
+    adi.step_static(CFD, nx, ny, 1.0 / nx, 0.5 / nx, adi.ADI_FP64, *ptrs)
+    torch.cuda.synchronize()
