@@ -1551,17 +1551,23 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
                 const int use = two ? (it >> 1) : it;
                 unsigned char *stage = fac_smem + (size_t)st * stage_bytes;
                 if (use > 0) {
-                    // the previous group of this stage is solved: write its outputs, then refill
+                    // the previous group of this stage is solved: write its outputs, then refill.
+                    // The copies that filled it have landed (the compute warps waited for them);
+                    // if a compute warp's wait ran out they may not have, so this lane waits for
+                    // them itself before it copies anything into the stage again.
                     if (!mbar_wait(&empty[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
+                    if (!mbar_wait(&full[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
                     fac_store_outputs<T>(stage);
                 }
                 fac_issue<T, BS, SPLIT>(descs, groups + gi, stage, &full[st]);
                 last[st] = use;
             }
-            // the last groups of each stage: wait until solved, write their outputs
+            // the last groups of each stage: wait until solved and until their copies have
+            // landed (no bulk copy into this CTA's shared memory may outlive it), write outputs
             for (int k = 0; k < 2; ++k)
                 if (last[k] >= 0) {
                     if (!mbar_wait(&empty[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
+                    if (!mbar_wait(&full[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
                     fac_store_outputs<T>(fac_smem + (size_t)k * stage_bytes);
                 }
             // global visibility of the output copies before the CTA ends
