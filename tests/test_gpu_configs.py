@@ -221,8 +221,9 @@ def test_fp64_convergence_ladder(adi, method, top):
 @pytest.mark.parametrize("method", [CFD, MFD])
 def test_8192_fp32_heterogeneous_one_step_against_fp64_line_solver(adi, method):
     """The 8192 x 8192 FP32 heterogeneous run (layered medium, centre Ricker; lines this long
-    take the chunked solver): smooth random fields advanced one step, against the FP64
-    thread-per-line solver on the same inputs, relative L2 <= 1e-4 per field."""
+    run as split lines in the factored solver, each cut into sub-lines with a halo of the scan
+    reach): smooth random fields advanced one step, against the FP64 thread-per-line solver on
+    the same inputs, relative L2 <= 1e-4 per field."""
     side = 8192
     rng = np.random.default_rng(8 + method)
     sp = wl.seismic_spec(method, side, side, 1, h=5.0, seed=3 + method)
