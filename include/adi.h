@@ -73,7 +73,10 @@ int adi_abi_version(void);
 const char *adi_strerror(int code);
 
 /*
- * adi_create -- one simulation resident on the current CUDA device.
+ * adi_create -- one simulation resident on the current CUDA device: the velocity-pressure
+ * system of Sec. 2, Eq. 1 (u_t = -kappa div(v,w) + f, rho (v,w)_t = -grad u) on nx x ny
+ * cells with Dirichlet pressure on the walls, discretised by Eq. 4 (CFD, nodal mesh of
+ * Sec. 2.1) or Eq. 12 (MFD, staggered mesh of Sec. 2.2; field placement as in Sec. 2.2).
  *   method     ADI_CFD or ADI_MFD.
  *   nx, ny     cells along x and y (16 .. 16384).
  *   h, dt      cell side and time step, both > 0 and finite.
@@ -130,13 +133,43 @@ size_t adi_state_bytes(int method, int nx, int ny, int precision);
  */
 int adi_set_source(adi_handle sim, int is, int js, double amp, double f0, double tdelay);
 
+/*
+ * adi_set_harmonic -- time-harmonic Dirichlet walls and a distributed forcing, the data of the
+ * manufactured problem of Sec. 4 (Eq. 11: u = Psi(x, y) cos(2 pi t / T) with its forcing):
+ *     u(t) = B cos(omega t + phase_b)   on U's outer rows and columns,
+ *     f(t) = F cos(omega t + phase_f)   at U's interior points (Eq. 1's forcing term),
+ * added to the carried state as Eqs. 6-7 add the source (dt/2 f(t_m) in stage 1, dt/2
+ * f(t_{m+1}) in stage 2), t = steps * dt.  The intermediate pressure u* on the ends of the
+ * x-lines (west and east walls) is taken at the half step, u(t_m + dt/2); the y-lines' ends
+ * (south and north walls) take u(t_{m+1}).  The paper does not state u*'s wall value; this
+ * reading gives the second-order convergence that Tables 4-5 report for Gamma != 0.
+ *   B   host, U's shape; only its outer rows and columns are read.  NULL: back to
+ *       time-independent walls (the values the fields hold at the call).
+ *   F   host, U's shape, or NULL for no forcing; only interior points are read.
+ * The current fields' walls are replaced by B cos(omega t_now + phase_b) and the carried state
+ * is rebuilt at the current time.  A point source (adi_set_source) may be combined with it.
+ * Velocities on the walls' own lines (v on the south/north rows, w on the west/east columns)
+ * are not advanced, as in the paper's algorithms (they never enter the pressure).
+ * Not used by adi_step_static or adi_fixed_point.  Device memory: the wall amplitudes and,
+ * with F, two copies of F in the carried layouts (not counted by adi_state_bytes).
+ * Errors: ADI_EINVAL (non-finite values, F without B), ADI_EBUSY in a batch, ADI_ENOMEM,
+ * ADI_ECUDA.
+ */
+int adi_set_harmonic(adi_handle sim, const double *B, const double *F, double omega,
+                     double phase_b, double phase_f);
+
 /* adi_set_stream -- CUDA stream (cudaStream_t, NULL = legacy default) for later calls. */
 int adi_set_stream(adi_handle sim, void *cuda_stream);
 
 /*
- * adi_step -- enqueue nsteps >= 0 full time steps (stage 1 then stage 2 each) on the
- * handle's stream.  Asynchronous: returns after launching.  For nsteps >= 2 the step
- * loop is captured once into a CUDA graph and replayed.
+ * adi_step -- enqueue nsteps >= 0 full time steps on the handle's stream.  Each step is the
+ * Peaceman-Rachford split of Eq. 5: stage 1 (Eq. 6) solves the coupled line system of Eq. 8
+ * on every interior x-line, stage 2 (Eq. 7) the system of Eq. 10 on every interior y-line,
+ * each exactly (the fixed point of Eq. 9).  Asynchronous: returns after launching.  For
+ * nsteps >= 2 the step loop is captured once into a CUDA graph and replayed.  The stream is
+ * the one set by adi_set_stream (the handle's own stream by default).
+ * Errors: ADI_EINVAL (nsteps < 0), ADI_EBUSY (member of a live batch or ticket), ADI_ECUDA,
+ * or the handle's sticky error.
  */
 int adi_step(adi_handle sim, int nsteps);
 
@@ -145,7 +178,10 @@ int adi_sync(adi_handle sim);
 
 /*
  * adi_read_fields -- synchronise and copy the current (U, V, W) into caller-owned host
- * buffers with the shapes above (any pointer may be NULL to skip that field).
+ * buffers with the shapes above (any pointer may be NULL to skip that field): pressure and
+ * the two velocity components of Eq. 1 at the mesh points of Sec. 2.1 (CFD: all on nodes) or
+ * Sec. 2.2 (MFD: pressure at cell centres and edges, v on x-faces, w on y-faces), at the
+ * handle's current time.  Errors: the handle's sticky error, ADI_ECUDA.
  */
 int adi_read_fields(adi_handle sim, double *u, double *v, double *w);
 
@@ -258,18 +294,27 @@ int adi_server_destroy(adi_server s);
  *   method, nx, ny, h, dt, precision   as for adi_create; nx, ny <= ADI_STATIC_MAX_CELLS.
  *   c, u, v, w            device arrays of the precision's type (float or double), row-major
  *                         with the shapes of adi_create (c at U's points, every value > 0,
- *                         not checked); u's outer rows/columns are the Dirichlet data.
+ *                         not checked); u's outer rows/columns are the Dirichlet data.  Each
+ *                         of the seven pointers must be device or managed memory of the
+ *                         current device (checked with cudaPointerGetAttributes: host memory
+ *                         gives ADI_EINVAL before any work is enqueued); their sizes are
+ *                         not checked.
  *   u_out, v_out, w_out   device arrays with the same shapes, each distinct from every
  *                         input and from each other; they receive the fields one step later.
  *   cuda_stream           the work runs on this stream (NULL = legacy default); the call
  *                         returns after it has finished.
  * Every temporary (line descriptors, tables, carried state, per-line solver scratch) lives in
- * one fixed-size array of device memory inside libadi.  The first call on a device looks up
- * that array's address with the device current; make that first call before any stream
- * capture begins.  Calls that overlap in time (several host threads, or several streams of
- * one device) share the array and race: serialise them.
+ * one fixed-size array of device memory inside libadi (4 MiB, held by every device that loads
+ * the library until the process exits).  The first call on a device looks up that array's
+ * address with the device current and keeps it; make that first call before any stream
+ * capture begins.  A cudaDeviceReset, or a driver context other than the device's primary
+ * one, invalidates the kept address: use the entry point only in processes that keep the
+ * primary context.  The call is synchronous: it returns once the step has finished on the
+ * stream.  Calls that overlap in time (several host threads, or several streams of one
+ * device) share the array and race: serialise them.
  * Errors: ADI_EINVAL (bad method/precision, sizes below ADI_MIN_CELLS, h or dt not > 0,
- * a NULL or aliased pointer); ADI_ENOMEM when nx or ny exceeds ADI_STATIC_MAX_CELLS (the
+ * a NULL, aliased, host or other-device pointer); ADI_ENOMEM when nx or ny exceeds
+ * ADI_STATIC_MAX_CELLS (the
  * array's capacity); ADI_ESINGULAR, ADI_ECUDA, ADI_ENOTSUP as elsewhere.
  */
 #define ADI_STATIC_MAX_CELLS 128
@@ -279,7 +324,10 @@ int adi_step_static(int method, int nx, int ny, double h, double dt, int precisi
 
 /*
  * adi_batch_submit -- runs simulations with their own step counts as one asynchronous batch
- * and returns at once with a ticket.  Every member with steps left advances together (one
+ * and returns at once with a ticket.  Each member advances by the Peaceman-Rachford steps of
+ * Eqs. 6-7 exactly as adi_step would; the paper notes that the line systems of one stage are
+ * independent of each other (Sec. 2.1, after Alg. 1), which is what lets one launch serve
+ * the lines of every member.  Every member with steps left advances together (one
  * persistent, graph-launched plan per phase over all their lines); a member whose count is
  * reached leaves and the others go on.  Until adi_batch_poll reports the ticket done, the
  * members are busy: adi_step, adi_set_solver, adi_set_source, adi_autotune, adi_batch_create,
@@ -320,6 +368,16 @@ int adi_batch_poll(int ticket, int *done);
 int adi_fixed_point(int method, int nx, int ny, double h, double dt, const double *c_field,
                     double *u, double *v, double *w, int nsteps, double t0, const double *source,
                     int kmax, double eps, int precision, long long *sweeps, double *device_ms);
+
+/*
+ * adi_fma_peak -- measured fused multiply-add throughput of the current device in FP64 or FP32
+ * (flop/s, counting an FMA as two), the denominator of the ALU roofline of the line solvers in
+ * that precision.  The paper has no counterpart: a measurement service.  A grid of 8 CTAs per
+ * SM, each thread 16 independent FMA chains; the best of three timed launches after a warm-up
+ * one, CUDA events on a stream of its own.  Allocates a small output buffer for the call.
+ * Changes no setting of the GPU.  Errors: ADI_EINVAL, ADI_ECUDA, ADI_ENOTSUP.
+ */
+int adi_fma_peak(int precision, double *flops_per_s);
 
 /*
  * adi_selftest_wait_timeout -- runs the failure path of the kernels' bounded waits on

@@ -61,6 +61,8 @@ _SIGS = {
     "adi_fixed_point": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp,
                          _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, ctypes.c_double,
                          ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp], ctypes.c_int),
+    "adi_set_harmonic": ([_vp, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "adi_fma_peak": ([ctypes.c_int, _dp], ctypes.c_int),
     "adi_step": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_sync": ([_vp], ctypes.c_int),
     "adi_read_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
@@ -130,6 +132,13 @@ def _arr(a, shape):
     if a.shape != tuple(shape):
         raise ValueError("expected shape %s, got %s" % (shape, a.shape))
     return a, a.ctypes.data_as(_dp)
+
+
+def fma_peak(precision):
+    """adi_fma_peak: the device's measured FMA throughput (flop/s) in FP64 or FP32."""
+    out = ctypes.c_double(0.0)
+    _check(lib().adi_fma_peak(int(precision), ctypes.byref(out)), "adi_fma_peak")
+    return out.value
 
 
 def step_static(method, nx, ny, h, dt, precision, c, u, v, w, u_out, v_out, w_out, stream=0):
@@ -216,6 +225,15 @@ class Sim:
 
     def set_source(self, is_, js, amp, f0, tdelay):
         _check(lib().adi_set_source(self._h, is_, js, amp, f0, tdelay), "adi_set_source")
+
+    def set_harmonic(self, B=None, F=None, omega=0.0, phase_b=0.0, phase_f=0.0):
+        """adi_set_harmonic: walls B cos(omega t + phase_b), forcing F cos(omega t + phase_f)
+        (arrays of U's shape); B=None returns to time-independent walls."""
+        su = self.shapes[0]
+        B, bp = _arr(B, su)
+        F, fp = _arr(F, su)
+        _check(lib().adi_set_harmonic(self._h, bp, fp, float(omega), float(phase_b), float(phase_f)),
+               "adi_set_harmonic")
 
     def set_stream(self, stream_ptr):
         _check(lib().adi_set_stream(self._h, _vp(stream_ptr)), "adi_set_stream")

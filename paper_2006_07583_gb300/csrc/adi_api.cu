@@ -192,6 +192,10 @@ struct Plan {
     DevBuf tdesc[2];
     int tcount[2] = {0, 0}, trows[2] = {0, 0}, tcols[2] = {0, 0};
     DevBuf fault;                            // set by a factored launch whose wait ran out
+    // time-harmonic walls and forcing of the members that have them (after each stage)
+    DevBuf hdesc;
+    int hcount = 0;
+    size_t hmax = 0;
     std::map<int, cudaGraphExec_t> graphs;
 };
 
@@ -223,6 +227,9 @@ void plan_free(Plan &p) {
     }
     dev_free(p.scratch);
     dev_free(p.fault);
+    dev_free(p.hdesc);
+    p.hcount = 0;
+    p.hmax = 0;
 }
 
 // ADI_ETIMEOUT if a launch of the plan gave up waiting for its staged inputs.
@@ -263,6 +270,11 @@ struct adi_sim {
     bool src_on = false;
     int src_i = 0, src_j = 0;
     double src_amp = 0, src_f0 = 0, src_td = 0;
+    // time-harmonic walls and forcing (adi_set_harmonic): wall amplitudes (FP64), F in both
+    // carried layouts (absent without forcing), and this simulation's own record on the device
+    bool harm_on = false;
+    double h_omega = 0, h_phb = 0, h_phf = 0;
+    DevBuf h_edges, h_frow, h_fcol, h_self;
 };
 
 struct adi_batch_t {
@@ -475,7 +487,8 @@ void fill_descs(adi_sim *s, int par, std::vector<LineDesc<T>> &rows, std::vector
         d.tab = tab + (size_t)(g.piy + c) * kTabLine;
         d.sep = sep ? sep + sep_off : nullptr;
         sep_off += rec_y;
-        if (s->src_on && s->src_j == j) { d.src_k = s->src_i; d.advance_clock = 1; }
+        // with harmonic data the clock advances after the stage's harmonic launch instead
+        if (s->src_on && s->src_j == j) { d.src_k = s->src_i; d.advance_clock = s->harm_on ? 0 : 1; }
     }
 }
 
@@ -487,6 +500,22 @@ void build_host_descs(adi_sim *s) {
         s->h_desc[par][0].assign((unsigned char *)rows.data(), (unsigned char *)(rows.data() + rows.size()));
         s->h_desc[par][1].assign((unsigned char *)cols.data(), (unsigned char *)(cols.data() + cols.size()));
     }
+}
+
+// The harmonic record of a simulation with time-harmonic walls (and forcing).
+HarmDesc harm_desc_of(const adi_sim *s) {
+    const Geometry &g = s->g;
+    HarmDesc d;
+    d.a_row = s->A[0].p;
+    d.c_col = s->A[1].p;
+    d.uo = s->Uo.p;
+    d.f_row = s->h_frow.p;
+    d.f_col = s->h_fcol.p;
+    d.edges = (const double *)s->h_edges.p;
+    d.clock = (long long *)s->clock.p;
+    d.rows_u = g.rows_u; d.ldu = g.ldu; d.lda = g.lda; d.ldc = g.ldc;
+    d.dt = s->dt; d.omega = s->h_omega; d.phb = s->h_phb; d.phf = s->h_phf;
+    return d;
 }
 
 // Builds an execution plan for members (all of one precision).  Plan parity q uses each
@@ -620,6 +649,21 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
         if (!rc) rc = cuda_status(cudaMemcpyAsync(p.tdesc[dir].p, td.data(), td.size() * sizeof(TDesc),
                                                   cudaMemcpyHostToDevice, stream));
     }
+    // the harmonic records of the members with time-harmonic walls
+    if (!rc) {
+        std::vector<HarmDesc> hd;
+        for (adi_sim *s : members)
+            if (s->harm_on) {
+                hd.push_back(harm_desc_of(s));
+                p.hmax = std::max(p.hmax, s->g.nU());
+            }
+        p.hcount = (int)hd.size();
+        if (!hd.empty()) {
+            rc = dev_alloc(p.hdesc, hd.size() * sizeof(HarmDesc));
+            if (!rc) rc = cuda_status(cudaMemcpyAsync(p.hdesc.p, hd.data(), hd.size() * sizeof(HarmDesc),
+                                                      cudaMemcpyHostToDevice, stream));
+        }
+    }
     if (!rc) rc = dev_alloc(p.fault, sizeof(int));
     if (!rc) rc = cuda_status(cudaMemsetAsync(p.fault.p, 0, sizeof(int), stream));
     if (!rc && (p.v1n[0] || p.v1n[1])) {
@@ -663,6 +707,9 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
         }
         e = cudaGetLastError();
     }
+    // time-harmonic walls and forcing, in the layout the next stage reads
+    if (e == cudaSuccess && p.hcount)
+        e = launch_harmonic<T>((const HarmDesc *)p.hdesc.p, p.hcount, p.hmax, dir, stream);
     return e;
 }
 
@@ -758,8 +805,35 @@ int run_prologue_t(adi_sim *s) {
     return rc;
 }
 
+// One launch of the harmonic kernel for this simulation alone (mode 2 or 3).
+int harm_self(adi_sim *s, int mode) {
+    if (!s->harm_on) return ADI_OK;
+    if (!s->h_self.p) {
+        int rc = dev_alloc(s->h_self, sizeof(HarmDesc));
+        if (rc) return rc;
+    }
+    const HarmDesc d = harm_desc_of(s);
+    cudaError_t e = cudaMemcpyAsync(s->h_self.p, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = s->precision == ADI_FP64 ? launch_harmonic<double>((const HarmDesc *)s->h_self.p, 1, s->g.nU(), mode, s->stream)
+                                     : launch_harmonic<float>((const HarmDesc *)s->h_self.p, 1, s->g.nU(), mode, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // d leaves scope
+    return cuda_status(e);
+}
+
+// Rebuilds the carried state from the natural fields; with time-harmonic data it then adds
+// dt/2 f(t_now) and sets the x-line ends to the coming step's u*.
 int prologue(adi_sim *s) {
-    return s->precision == ADI_FP64 ? run_prologue_t<double>(s) : run_prologue_t<float>(s);
+    int rc = s->precision == ADI_FP64 ? run_prologue_t<double>(s) : run_prologue_t<float>(s);
+    if (!rc) rc = harm_self(s, 3);
+    return rc;
+}
+
+// The device step clock follows the host's step count (sources and harmonic data read it).
+int sync_clock(adi_sim *s) {
+    cudaError_t e = cudaMemcpyAsync(s->clock.p, &s->steps, sizeof(long long), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_status(e);
 }
 
 template <typename T>
@@ -856,6 +930,8 @@ int load_state(adi_sim *s, const double *u, const double *v, const double *w, bo
     if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nVp() * esz, cudaMemcpyDeviceToDevice, s->stream));
     if (!rc && (u || !keep_missing)) rc = upload(s, u, s->Uo.p, g.rows_u, g.ldu, g.ldu, (double *)staging.p, 1.0, 0);
     if (!rc && (w || !keep_missing)) rc = upload(s, w, s->Wo.p, g.rows_w, g.ldw, g.ldw, (double *)staging.p, 1.0, 0);
+    // with time-harmonic walls, u's walls are the harmonic data at the current time
+    if (!rc) rc = harm_self(s, 2);
     // all four carried-pressure arrays start from u (their outer rows/columns stay the
     // Dirichlet data: line kernels write interior lines only)
     for (int k = 0; k <= 2 && !rc; k += 2)
@@ -1145,6 +1221,70 @@ int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_pe
     return ADI_OK;
 }
 
+int adi_set_harmonic(adi_handle s, const double *B, const double *F, double omega, double phase_b,
+                     double phase_f) {
+    if (!s) return ADI_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (s->in_batch) return ADI_EBUSY;
+    if (!std::isfinite(omega) || !std::isfinite(phase_b) || !std::isfinite(phase_f)) return ADI_EINVAL;
+    const Geometry &g = s->g;
+    if (F && !B) return ADI_EINVAL;
+    if ((B && !all_finite(B, g.nU())) || (F && !all_finite(F, g.nU()))) return ADI_EINVAL;
+    if (!B && !s->harm_on) return ADI_OK;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->sticky = cuda_status(e);
+    int rc = ADI_OK;
+    if (!B) {  // back to time-independent walls: the ones the fields hold now
+        s->harm_on = false;
+        dev_free(s->h_edges); dev_free(s->h_frow); dev_free(s->h_fcol); dev_free(s->h_self);
+    } else {
+        // the wall amplitudes, kept in FP64: west, east (one per row), south, north (per column)
+        std::vector<double> ed(2 * (size_t)g.rows_u + 2 * (size_t)g.ldu);
+        for (int i = 0; i < g.rows_u; ++i) {
+            ed[i] = B[(size_t)i * g.ldu];
+            ed[g.rows_u + i] = B[(size_t)i * g.ldu + g.ldu - 1];
+        }
+        for (int j = 0; j < g.ldu; ++j) {
+            ed[2 * (size_t)g.rows_u + j] = B[j];
+            ed[2 * (size_t)g.rows_u + g.ldu + j] = B[(size_t)(g.rows_u - 1) * g.ldu + j];
+        }
+        if (!s->h_edges.p) rc = dev_alloc(s->h_edges, ed.size() * sizeof(double));
+        if (!rc) rc = cuda_status(cudaMemcpyAsync(s->h_edges.p, ed.data(), ed.size() * sizeof(double),
+                                                  cudaMemcpyHostToDevice, s->stream));
+        if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));  // ed leaves scope
+        if (!rc && F) {  // F in the layouts of both stages' carried pressure
+            if (!s->h_frow.p) rc = dev_alloc(s->h_frow, g.nA() * s->esz);
+            if (!rc && !s->h_fcol.p) rc = dev_alloc(s->h_fcol, g.nC() * s->esz);
+            if (!rc) rc = cuda_status(cudaMemsetAsync(s->h_frow.p, 0, g.nA() * s->esz, s->stream));
+            if (!rc) rc = cuda_status(cudaMemsetAsync(s->h_fcol.p, 0, g.nC() * s->esz, s->stream));
+            if (!rc) rc = xfer_buffer(s);
+            if (!rc) rc = upload(s, F, s->h_frow.p, g.rows_u, g.ldu, g.lda, (double *)s->xfer.p, 1.0, 0);
+            if (!rc) rc = transpose(s, s->h_frow.p, g.rows_u, g.ldu, g.lda, s->h_fcol.p, g.ldc);
+            if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
+        } else if (!rc) {
+            dev_free(s->h_frow); dev_free(s->h_fcol);
+        }
+        if (!rc) {
+            s->harm_on = true;
+            s->h_omega = omega; s->h_phb = phase_b; s->h_phf = phase_f;
+        }
+    }
+    // descriptors (who advances the clock), the plan (its harmonic records), then the state:
+    // walls at the current time, carried state rebuilt from the current fields
+    if (!rc) {
+        if (s->precision == ADI_FP64) build_host_descs<double>(s); else build_host_descs<float>(s);
+        rc = sync_clock(s);
+    }
+    if (!rc) rc = upload_sim_descs(s);
+    if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
+    s->plan_base = s->parity;
+    if (!rc) rc = load_state(s, nullptr, nullptr, nullptr, true);
+    dev_free(s->xfer);
+    dev_free(s->pro);
+    if (rc) s->sticky = rc;
+    return rc;
+}
+
 int adi_set_stream(adi_handle s, void *stream) {
     if (!s) return ADI_EINVAL;
     if (s->own_stream) { cudaStreamSynchronize(s->stream); cudaStreamDestroy(s->stream); s->own_stream = false; }
@@ -1165,7 +1305,8 @@ int adi_set_source(adi_handle s, int is, int js, double amp, double f0, double t
     s->src_on = true; s->src_i = is; s->src_j = js;
     s->src_amp = amp; s->src_f0 = f0; s->src_td = tdelay;
     if (s->precision == ADI_FP64) build_host_descs<double>(s); else build_host_descs<float>(s);
-    int rc = upload_sim_descs(s);
+    int rc = sync_clock(s);  // the source is evaluated at the current step's time
+    if (!rc) rc = upload_sim_descs(s);
     if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
     s->plan_base = s->parity;
     if (!rc) rc = prologue(s);  // a picks up dt/2 f(t_now) at the source point
@@ -1282,7 +1423,7 @@ int adi_destroy(adi_handle s) {
     plan_free(s->plan);
     DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->A[2], &s->A[3], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
                       &s->alphaT, &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status,
-                      &s->xfer, &s->pro};
+                      &s->xfer, &s->pro, &s->h_edges, &s->h_frow, &s->h_fcol, &s->h_self};
     for (DevBuf *b : bufs) dev_free(*b);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     (void)cudaGetLastError();

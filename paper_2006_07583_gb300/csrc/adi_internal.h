@@ -70,6 +70,24 @@ cudaError_t launch_finite_check(const T *x, size_t n, int *flag, cudaStream_t s)
 // Scratch words per line of the thread-per-line solver (solution + block factors).
 size_t v1_scratch_words(int method, int N);
 
+// Time-harmonic walls and forcing (adi_harmonic.cu): one record per simulation that has them.
+// Walls u = B cos(omega t + phb); forcing f = F cos(omega t + phf); t = clock * dt.
+struct HarmDesc {
+    void *a_row;          // carried a, row-major (leading dimension lda): the x-lines' input
+    void *c_col;          // carried C, column-major (leading dimension ldc): the y-lines' input
+    void *uo;             // natural pressure, row-major rows_u x ldu
+    const void *f_row;    // F at U's points, row-major (lda), or nullptr (no forcing)
+    const void *f_col;    // F column-major (ldc), or nullptr
+    const double *edges;  // B on the walls: west [rows_u], east [rows_u], south [ldu], north [ldu]
+    long long *clock;     // completed steps of the simulation
+    int rows_u, ldu, lda, ldc;
+    double dt, omega, phb, phf;
+};
+// mode 0: after stage 1; 1: after stage 2 (advances the clocks); 2: the natural walls at the
+// clock's time; 3: the carried state after a prologue.  max_points: the largest rows_u * ldu.
+template <typename T>
+cudaError_t launch_harmonic(const HarmDesc *d, int n, size_t max_points, int mode, cudaStream_t s);
+
 // Factored solver (adi_factored.cu).
 // One line group of a launch, built on the host: lines [first, first + nl) of one simulation
 // and direction, with the geometry every thread of the CTA needs; or, for a line with more

@@ -1,0 +1,175 @@
+"""GPU parity of the time-harmonic walls and forcing (adi_set_harmonic; the problem of Sec. 4,
+Eq. 11) against the oracle's harmonic mode, and the paper's Gamma != 0 convergence on the GPU.
+
+* Random walls B, forcing F, frequency and phases, random media and fields: FP64 <= 1e-12 of
+  max |field|, FP32 relative L2 <= 1e-4, every solver, with and without a point source.
+* Harmonic data switched on after some steps (the walls and the forcing follow the step clock).
+* A batch mixing harmonic and plain members equals its members run alone.
+* The manufactured solution of Eq. 11 with Gamma = k = 9 (lambda = 1/4, T = 1/sqrt(2),
+  dt = cfl_max h) in FP64: error falls at rate about 2, the trend of Tables 4-5 for Gamma != 0.
+  MFD from N = 64 to 1024; CFD to 96 only, over t = 0.25, because its growing modes
+  (test_oracle_stability.py) take over on finer grids.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_07583_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+CFD, MFD = wl.CFD, wl.MFD
+
+
+@pytest.fixture(scope="module")
+def adi():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_07583_gb300 import adi as _adi
+
+    _adi.lib()
+    return _adi
+
+
+def _max_rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def _l2_rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _case(method, nx, ny, seed, force=True):
+    rng = np.random.default_rng(seed)
+    su, sv, sw = wl.shapes(method, nx, ny)
+    h = 1.0 / max(nx, ny)
+    c = rng.uniform(0.6, 1.4, su)
+    B = rng.standard_normal(su)
+    F = rng.standard_normal(su) * 5.0 if force else None
+    om, pb, pf = 9.1, 0.3, -0.8
+    U = rng.standard_normal(su)
+    U[0, :] = B[0, :] * math.cos(pb); U[-1, :] = B[-1, :] * math.cos(pb)
+    U[:, 0] = B[:, 0] * math.cos(pb); U[:, -1] = B[:, -1] * math.cos(pb)
+    V, W = rng.standard_normal(sv), rng.standard_normal(sw)
+    return h, 0.8 * h / c.max(), c, U, V, W, B, F, om, pb, pf
+
+
+def _check(G, O, precision):
+    for g, o in zip(G, O):
+        if precision == 1:
+            assert _max_rel(g, o) <= 1e-12, _max_rel(g, o)
+        else:
+            assert _l2_rel(g, o) <= 1e-4, _l2_rel(g, o)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("solver", [0, 1, 2])
+@pytest.mark.parametrize("method,nx,ny", [(CFD, 24, 19), (MFD, 17, 30), (CFD, 230, 171), (MFD, 260, 97)])
+def test_harmonic_vs_oracle(adi, method, nx, ny, solver, precision):
+    h, dt, c, U, V, W, B, F, om, pb, pf = _case(method, nx, ny, seed=nx + 7 * ny + method)
+    steps = 4
+    s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=precision, solver=solver)
+    s.set_harmonic(B, F, om, pb, pf)
+    s.step(steps)
+    G = s.read()
+    s.close()
+    O = oracle.run_harmonic(method, nx, ny, h, dt, c ** 2, U, V, W, steps, B, F, om, pb, pf,
+                            threads=max(1, oracle.num_threads()))
+    _check(G, O, precision)
+
+
+@pytest.mark.parametrize("method", [CFD, MFD])
+def test_harmonic_with_source_and_late_start(adi, method):
+    """Three plain steps, then walls, forcing and a Ricker source from t = 3 dt on."""
+    nx, ny = 40, 33
+    h, dt, c, U, V, W, B, F, om, pb, pf = _case(method, nx, ny, seed=5 + method)
+    src = (ny // 2, nx // 2, 0.9, 11.0, 0.02)
+    s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=adi.ADI_FP64)
+    s.step(3)
+    s.set_harmonic(B, F, om, pb, pf)
+    s.set_source(*src)
+    s.step(4)
+    G = s.read()
+    s.close()
+    O = oracle.run(method, nx, ny, h, dt, c ** 2, U, V, W, 3)
+    t3 = 3 * dt
+    Uw = O[0].copy()
+    wall = B * math.cos(om * t3 + pb)
+    Uw[0, :] = wall[0, :]; Uw[-1, :] = wall[-1, :]; Uw[:, 0] = wall[:, 0]; Uw[:, -1] = wall[:, -1]
+    O = oracle.run_harmonic(method, nx, ny, h, dt, c ** 2, Uw, O[1], O[2], 4, B, F, om, pb, pf,
+                            t0=t3, source=src)
+    _check(G, O, 1)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_batch_with_harmonic_members_equals_alone(adi, precision):
+    specs = [(CFD, 30, 41, True), (MFD, 50, 20, False), (MFD, 33, 33, True), (CFD, 64, 17, False)]
+    cases = [_case(m, nx, ny, seed=90 + k) for k, (m, nx, ny, _) in enumerate(specs)]
+
+    def make(k):
+        (m, nx, ny, harm), (h, dt, c, U, V, W, B, F, om, pb, pf) = specs[k], cases[k]
+        s = adi.Sim(m, nx, ny, h, dt, c, U, V, W, precision=precision)
+        if harm:
+            s.set_harmonic(B, F, om, pb, pf)
+        return s
+
+    alone = []
+    for k in range(len(specs)):
+        s = make(k)
+        s.step(5)
+        alone.append(s.read())
+        s.close()
+    sims = [make(k) for k in range(len(specs))]
+    b = adi.Batch(sims)
+    b.step(5)
+    b.sync()
+    for s, ref in zip(sims, alone):
+        for x, y in zip(s.read(), ref):
+            assert np.array_equal(x, y)
+    b.close()
+    for s in sims:
+        s.close()
+
+
+def test_harmonic_off_returns_to_fixed_walls(adi):
+    """adi_set_harmonic(NULL) keeps the walls the fields hold at that moment, fixed."""
+    method, nx, ny = MFD, 30, 26
+    h, dt, c, U, V, W, B, F, om, pb, pf = _case(method, nx, ny, seed=61)
+    s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=adi.ADI_FP64)
+    s.set_harmonic(B, F, om, pb, pf)
+    s.step(2)
+    s.set_harmonic(None)
+    mid = s.read()
+    s.step(3)
+    G = s.read()
+    s.close()
+    O = oracle.run(method, nx, ny, h, dt, c ** 2, *mid, 3, t0=2 * dt)
+    _check(G, O, 1)
+
+
+def _eq11_gpu_error(adi, method, N, tsim):
+    P = wl.HarmonicProblem(method, N, 9.0, 9, 0.25, 1.0 / math.sqrt(2.0))
+    h = 1.0 / N
+    steps = int(round(tsim / wl.cfl_dt(method, h, 1.0)))
+    dt = tsim / steps
+    U, V, W = P.fields(0.0)
+    B, F, om, pb, pf = P.amplitudes()
+    s = adi.Sim(method, N, N, h, dt, wl.unit_kappa(method, N, N), U, V, W, precision=adi.ADI_FP64)
+    s.set_harmonic(B, F, om, pb, pf)
+    s.step(steps)
+    G = s.read()
+    s.close()
+    Ue, _, _ = P.fields(steps * dt)
+    return h * np.linalg.norm(G[0] - Ue)
+
+
+@pytest.mark.parametrize("method,Ns", [(MFD, [64, 128, 256, 512, 1024]), (CFD, [16, 24, 32, 48, 64, 96])])
+def test_eq11_gamma9_rate_about_two_on_gpu(adi, method, Ns):
+    errs = [_eq11_gpu_error(adi, method, N, 0.25) for N in Ns]
+    r = oracle.rates(errs, Ns)
+    assert 1.5 < oracle.trimmed_mean(r) < 2.8, (errs, r)
+    assert 1.3 < r[-1] < 2.8, (errs, r)
