@@ -72,6 +72,12 @@ def _load():
             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
         ]
         lib.oracle_run_harmonic.restype = ctypes.c_int
+        lib.oracle_run_sponge.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+            dp, dp, dp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
+            ctypes.c_int,
+        ]
+        lib.oracle_run_sponge.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -174,6 +180,26 @@ def run_harmonic(method, nx, ny, h, dt, kappa, U, V, W, nsteps, B, F=None, omega
                                      float(eps), int(threads))
     if rc:
         raise RuntimeError("oracle_run_harmonic failed: %d" % rc)
+    return U, V, W
+
+
+def run_sponge(method, nx, ny, h, dt, kappa, U, V, W, nsteps, width, a, t0=0.0, source=None,
+               threads=1):
+    """run() with Cerjan absorbing layers: after every step the fields at points within
+    `width` cells of a wall (distance delta) are multiplied by exp(-(a (width - delta))^2);
+    the pressure's own wall values are left alone."""
+    su, sv, sw = field_shapes(method, nx, ny)
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    V = np.array(V, dtype=np.float64, order="C", copy=True)
+    W = np.array(W, dtype=np.float64, order="C", copy=True)
+    assert kappa.shape == su and U.shape == su and V.shape == sv and W.shape == sw
+    src = None if source is None else np.array(source, dtype=np.float64)
+    rc = _load().oracle_run_sponge(method, nx, ny, h, dt, _ptr(kappa), _ptr(U), _ptr(V), _ptr(W),
+                                   int(nsteps), float(t0), _ptr(src) if src is not None else None,
+                                   float(width), float(a), int(threads))
+    if rc:
+        raise RuntimeError("oracle_run_sponge failed: %d" % rc)
     return U, V, W
 
 

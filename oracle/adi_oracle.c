@@ -768,9 +768,56 @@ static int pr_step(grid_t *g, const double *kappa, double *U, double *V, double 
  * sweeps: NULL, or 2 * nsteps ints that receive, per step, the fixed-point sweeps that
  * stage 1 and stage 2 took (kmax > 0 only; left untouched for exact solves).
  * Returns 0, -1 for invalid arguments, -2 for a singular line system. */
+/* ------------------------------------------------------------------------------------ */
+/* Absorbing layers: Cerjan's damping (named in Sec. 2.1 as the absorbing technique the    */
+/* CFD formulation admits).  After every full step each field value at a point whose       */
+/* distance to the nearest wall is delta cells, delta < width, is multiplied by            */
+/*     g = exp(-(a (width - delta))^2);                                                    */
+/* pressure values on the walls themselves (the Dirichlet data) are left alone.            */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct { double width, a; } sponge_t;
+
+/* Coordinates in cells of the points of U (kind 0), V (1), W (2) along x (row index j) and
+ * y (row index i): CFD nodes; MFD cell centres plus edges for pressure, nodes across the
+ * velocity's own direction. */
+static double coord(int method, int kind_axis_staggered, int k, int n) {
+    if (method == OR_CFD || !kind_axis_staggered) return (double)k;
+    if (k == 0) return 0.0;
+    if (k == n + 1) return (double)n;
+    return k - 0.5;
+}
+
+static double sponge_g(const sponge_t *sp, double x, double y, int nx, int ny) {
+    double d = x;
+    if (nx - x < d) d = nx - x;
+    if (y < d) d = y;
+    if (ny - y < d) d = ny - y;
+    if (d >= sp->width) return 1.0;
+    double q = sp->a * (sp->width - d);
+    return exp(-q * q);
+}
+
+static void sponge_apply(const grid_t *g, const sponge_t *sp, double *U, double *V, double *W) {
+    const int nx = g->nx, ny = g->ny, m = g->method;
+    /* U: staggered (MFD centres) along both axes; walls excluded */
+    for (int i = 1; i < g->rows_u - 1; ++i)
+        for (int j = 1; j < g->ldu - 1; ++j)
+            U[(size_t)i * g->ldu + j] *= sponge_g(sp, coord(m, 1, j, nx), coord(m, 1, i, ny), nx, ny);
+    /* V: x on nodes, y staggered (MFD) */
+    for (int i = 0; i < g->rows_v; ++i)
+        for (int j = 0; j < g->ldv; ++j)
+            V[(size_t)i * g->ldv + j] *= sponge_g(sp, (double)j, coord(m, 1, i, ny), nx, ny);
+    /* W: x staggered (MFD), y on nodes */
+    for (int i = 0; i < g->rows_w; ++i)
+        for (int j = 0; j < g->ldw; ++j)
+            W[(size_t)i * g->ldw + j] *= sponge_g(sp, coord(m, 1, j, nx), (double)i, nx, ny);
+}
+
 static int run_all(int method, int nx, int ny, double h, double dt, const double *kappa,
                    double *U, double *V, double *W, int nsteps, double t0, const double *src,
-                   const harm_t *hb, int kmax, double eps, int nthreads, int *sweeps) {
+                   const harm_t *hb, int kmax, double eps, int nthreads, int *sweeps,
+                   const sponge_t *sponge) {
     if ((method != OR_CFD && method != OR_MFD) || nx < 8 || ny < 8 || !(h > 0.0) ||
         !(dt > 0.0) || nsteps < 0 || kmax < 0)
         return -1;
@@ -784,10 +831,12 @@ static int run_all(int method, int nx, int ny, double h, double dt, const double
         if (s.is < lo || s.is > hiy || s.js < lo || s.js > hix) { grid_free(&g); return -1; }
     }
     int rc = 0;
-    for (int m = 0; m < nsteps && rc == 0; ++m)
+    for (int m = 0; m < nsteps && rc == 0; ++m) {
         if (pr_step(&g, kappa, U, V, W, t0 + m * dt, &s, hb, kmax, eps, nthreads,
                     sweeps ? sweeps + 2 * m : NULL))
             rc = -2;
+        if (sponge && rc == 0) sponge_apply(&g, sponge, U, V, W);
+    }
     grid_free(&g);
     return rc;
 }
@@ -796,7 +845,18 @@ int oracle_run(int method, int nx, int ny, double h, double dt, const double *ka
                double *U, double *V, double *W, int nsteps, double t0, const double *src,
                int kmax, double eps, int nthreads, int *sweeps) {
     return run_all(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0, src, NULL, kmax, eps,
-                   nthreads, sweeps);
+                   nthreads, sweeps, NULL);
+}
+
+/* oracle_run with Cerjan absorbing layers of `width` cells and strength `a` along every wall
+ * (width 0 or a 0: no damping). */
+int oracle_run_sponge(int method, int nx, int ny, double h, double dt, const double *kappa,
+                      double *U, double *V, double *W, int nsteps, double t0, const double *src,
+                      double width, double a, int nthreads) {
+    if (!(width >= 0.0) || !(a >= 0.0)) return -1;
+    sponge_t sp = {width, a};
+    return run_all(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0, src, NULL, 0, 0.0,
+                   nthreads, NULL, &sp);
 }
 
 /* oracle_run with time-harmonic Dirichlet data and forcing (Sec. 4, Eq. 11):
@@ -813,7 +873,7 @@ int oracle_run_harmonic(int method, int nx, int ny, double h, double dt, const d
     if (!B) return -1;
     harm_t hb = {B, F, omega, phb, phf};
     return run_all(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0, src, &hb, kmax, eps,
-                   nthreads, NULL);
+                   nthreads, NULL, NULL);
 }
 
 int oracle_num_threads(void) {
