@@ -53,7 +53,14 @@ def parse():
     ap.add_argument("--no-paper", action="store_true", help="skip the paper's fixed-point iteration leg")
     ap.add_argument("--ref-budget", type=float, default=REF_BUDGET_S,
                     help="seconds of oracle work the reference arm aims at")
-    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the config-4 serving stream (sides 64-4096, 100-5000 steps)")
+    ap.add_argument("--no-serve-fp64", action="store_true",
+                    help="skip the FP64 one-at-a-time comparator of the serving leg")
+    ap.add_argument("--no-batch256", action="store_true", help="skip the 256-simulation batch leg")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner leg")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="arithmetic of the main batched leg (fp64: the profiling case of the FP64 kernels)")
     ap.add_argument("--solver", default="default", choices=["default", "line", "chunked", "factored"],
                     help="line solver of the FP32 batch (default: the library's choice)")
     return ap.parse_args()
@@ -297,7 +304,8 @@ def main():
     sims = []
     for sp in specs:
         kw = {} if args.solver == "default" else {"solver": getattr(adi, "ADI_SOLVER_" + args.solver.upper())}
-        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32, **kw)
+        prec = adi.ADI_FP64 if args.precision == "fp64" else adi.ADI_FP32
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=prec, **kw)
         s.set_source(*sp.source.as_tuple())
         sims.append(s)
     batch = adi.Batch(sims)
@@ -344,12 +352,13 @@ def main():
     # each stage reads the carried pressure, the velocity and alpha and writes the first two
     # -> 5 words per grid point (20 B in FP32) over both simulations.
     peak, peak_kind = measured_peaks()
-    alg_bytes = 5 * 4 * pts
+    esz = 8 if args.precision == "fp64" else 4
+    alg_bytes = 5 * esz * pts
     avg1, avg2 = float(np.mean(st1)), float(np.mean(st2))
     dom_stage = 1 if solve_ms[1] >= solve_ms[2] else 2
     dom_ms = solve_ms[dom_stage]
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-    tpp = ncu_traffic_per_point()
+    tpp = ncu_traffic_per_point() if esz == 4 else None  # the committed figure is the FP32 kernels'
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": (tpp * pts if tpp is not None else None),
             "kernel": "line_solve_factored_kernel (stage %d, CFD + MFD launches)" % dom_stage,
@@ -361,9 +370,10 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "batched FP32 PR-ADI, 1 CFD + 1 MFD seismic sim at "
-                                  "%dx%d cells" % (args.side, args.side),
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if esz == 8 else "f32",
+           "data": "synthetic",
+           "config": {"workload": "batched %s PR-ADI, 1 CFD + 1 MFD seismic sim at "
+                                  "%dx%d cells" % (args.precision.upper(), args.side, args.side),
                       "global_batch": 2 * ws, "side": args.side,
                       "parallelism": "replicas x%d" % ws, "l2": "inputs larger than L2",
                       "h_m": 5.0, "source": "15 Hz Ricker",
@@ -377,11 +387,17 @@ def main():
         out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3))
     if rank == 0 and not args.no_fp64:
         out["fp64_plain"] = fp64_plain(adi, args.side)
-    if rank == 0 and not args.no_serve:
-        out["serving"] = serving_leg(adi, args.serve_requests, value)
     batch.close()
     for s in sims:
         s.close()
+    if rank == 0 and not args.no_fp64:
+        out["fp64_factored"] = fp64_factored_leg(adi, torch, args.side, peak)
+    if rank == 0 and not args.no_batch256:
+        out["batch256"] = batch256_leg(adi, torch, peak)
+    if rank == 0 and not args.no_serve:
+        out["serving"] = serving_leg(adi, args.serve_requests, not args.no_serve_fp64)
+    if rank == 0 and not args.no_tune:
+        out["autotune"] = tune_leg(adi)
     if rank == 0 and not args.no_peak:
         out["peak_8192"] = peak_leg(adi, torch, 8192, 20, peak)
     if rank == 0 and not args.no_paper:
@@ -490,61 +506,202 @@ def e2e_leg(adi, torch, sims, batch, specs, n):
             "d2h_bytes_per_step": h2d, "steps": n}
 
 
-def serving_leg(adi, n_req, capacity):
-    """The serving loop (adi_server_*) on a seeded Poisson request stream, scaled to finish in
-    seconds: square grids log-uniform in [64, 1024], 100-1000 steps, CFD/MFD 50/50, FP32, HBM
-    budget 150 GB; arrival rate set to an offered load of 0.8 x the batched capacity measured
-    above.  Reports p50/p99 latency (submission to completion), serving throughput, and the
-    plain one-simulation-at-a-time FP64 path on the first requests of the same stream."""
-    from paper_2006_07583_gb300 import workloads as wl
-
-    probe = wl.serving_stream(n_req, 1.0, seed=3, lo=64, hi=1024, steps_lo=100, steps_hi=1000)
-    mean_work = float(np.mean([r.spec.points * r.spec.steps for r in probe]))
-    rate = 0.8 * capacity / mean_work
-    reqs = wl.serving_stream(n_req, rate, seed=3, lo=64, hi=1024, steps_lo=100, steps_hi=1000)
-    srv = adi.Server(150 << 30, precision=adi.ADI_FP32, quantum=100, max_active=64)
+def _run_server(adi, reqs, arrivals, budget=150 << 30):
+    """One pass of the serving loop over `reqs` arriving at `arrivals` (seconds from the start):
+    returns (wall seconds, latencies in ms from submission to completion)."""
+    srv = adi.Server(budget, precision=adi.ADI_FP32, quantum=100, max_active=64)
+    order = sorted(range(len(reqs)), key=lambda k: arrivals[k])
     tickets = []
     t0 = time.perf_counter()
     nxt, running, pending = 0, 0, 0
     while True:
         now = time.perf_counter() - t0
-        while nxt < len(reqs) and reqs[nxt].arrival <= now:
-            sp = reqs[nxt].spec
+        submitted = False
+        while nxt < len(order) and arrivals[order[nxt]] <= now:
+            sp = reqs[order[nxt]].spec
             tickets.append(srv.submit(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, sp.steps,
                                       source=sp.source.as_tuple()))
             nxt += 1
-        if running or pending:
+            submitted = True
+        if running or pending or submitted:
             running, pending = srv.tick()
-        elif nxt < len(reqs):
-            time.sleep(max(0.0, min(0.01, reqs[nxt].arrival - now)))
-            running, pending = srv.tick()
+        elif nxt < len(order):
+            time.sleep(max(0.0, min(0.01, arrivals[order[nxt]] - now)))
         else:
             break
     wall = time.perf_counter() - t0
     lat = []
     for t in tickets:
-        st, ts, _t0, t1 = srv.status(t)
-        lat.append(1e3 * (t1 - ts))
+        _st, ts, _ta, td = srv.status(t)
+        lat.append(1e3 * (td - ts))
     srv.close()
-    work = sum(r.spec.points * r.spec.steps for r in reqs)
-    # plain path: FP64, thread-per-line solver, one simulation at a time, on the first requests
-    n_plain = min(6, len(reqs))
-    tp = 0.0
-    for r in reqs[:n_plain]:
+    return wall, lat
+
+
+def _one_at_a_time(adi, reqs, precision):
+    """Every request alone, one after the other, with the library's default solver: create,
+    source, steps, read the fields back, destroy -- the same per-request work the serving loop
+    does (creation at admission, results read at retirement).  Wall-clock seconds."""
+    t0 = time.perf_counter()
+    for r in reqs:
         sp = r.spec
-        tq = time.perf_counter()
-        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP64, solver=adi.ADI_SOLVER_LINE)
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=precision)
         s.set_source(*sp.source.as_tuple())
         s.step(sp.steps)
-        s.sync()
+        s.read()
         s.close()
-        tp += time.perf_counter() - tq
-    plain = sum(r.spec.points * r.spec.steps for r in reqs[:n_plain]) / tp
-    return {"requests": len(reqs), "offered_rate_per_s": rate, "wall_s": wall, "value": work / wall,
-            "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "plain_fp64_one_at_a_time": {"value": plain, "unit": UNIT, "requests": n_plain},
-            "workload": "Poisson stream, sides log-uniform 64-1024, 100-1000 steps, CFD/MFD, FP32, "
-                        "150 GB budget, quantum 100 steps"}
+    return time.perf_counter() - t0
+
+
+def serving_leg(adi, n_req, with_fp64=True):
+    """The serving loop (adi_server_*) on the config-4 request stream: square grids with sides
+    log-uniform in [64, 4096], 100-5000 steps, CFD/MFD 50/50, FP32, 150 GB HBM budget, seeded
+    Poisson arrivals.  Capacity is the throughput with every request submitted at once; the
+    offered load is then swept over 0.5, 0.8, 1.0 and 1.2 x capacity (same requests, arrival
+    times of one seeded Poisson stream scaled to the rate).  Comparators on the same full
+    request set: the default (factored) solver one simulation at a time in FP32 -- isolating
+    what continuous batching gains -- and in FP64, the plain one-at-a-time FP64 path."""
+    from paper_2006_07583_gb300 import workloads as wl
+
+    reqs = wl.serving_stream(n_req, 1.0, seed=3)  # arrivals at rate 1/s, rescaled below
+    work = float(sum(r.spec.points * r.spec.steps for r in reqs))
+    mean_work = work / len(reqs)
+    wall_sat, lat_sat = _run_server(adi, reqs, [0.0] * len(reqs))
+    capacity = work / wall_sat
+    loads = {}
+    for f in (0.5, 0.8, 1.0, 1.2):
+        rate = f * capacity / mean_work
+        wall, lat = _run_server(adi, reqs, [r.arrival / rate for r in reqs])
+        loads["%.1f" % f] = {"offered_rate_per_s": rate, "wall_s": wall, "value": work / wall,
+                             "p50_ms": float(np.percentile(lat, 50)),
+                             "p99_ms": float(np.percentile(lat, 99))}
+    out = {"requests": len(reqs), "updates": work, "unit": UNIT,
+           "capacity": {"value": capacity, "wall_s": wall_sat, "p50_ms": float(np.percentile(lat_sat, 50)),
+                        "p99_ms": float(np.percentile(lat_sat, 99))},
+           "loads": loads,
+           # headline: throughput at saturation (comparable with the one-at-a-time arms, which
+           # also run back to back), latency at an offered load of 0.8 x capacity
+           "value": capacity, "p50_ms": loads["0.8"]["p50_ms"], "p99_ms": loads["0.8"]["p99_ms"],
+           "workload": "config 4: Poisson stream of %d requests, sides log-uniform 64-4096, 100-5000 "
+                       "steps, CFD/MFD, FP32, 150 GB budget, quantum 100 steps" % len(reqs)}
+    t32 = _one_at_a_time(adi, reqs, adi.ADI_FP32)
+    out["fp32_one_at_a_time"] = {"value": work / t32, "unit": UNIT, "wall_s": t32, "requests": len(reqs)}
+    if with_fp64:
+        t64 = _one_at_a_time(adi, reqs, adi.ADI_FP64)
+        out["fp64_one_at_a_time"] = {"value": work / t64, "unit": UNIT, "wall_s": t64, "requests": len(reqs)}
+    return out
+
+
+def tune_leg(adi, sides=(256, 1024, 4096)):
+    """adi_autotune on single FP32 seismic simulations per size class: ms per step of every
+    solver with the automatic launch, and of the factored solver with the launch parameters the
+    tuner keeps (lines per CTA cap, ring depth cap; 0 = automatic)."""
+    from paper_2006_07583_gb300 import workloads as wl
+
+    names = {0: "line", 1: "chunked", 2: "factored"}
+    out = {}
+    for side in sides:
+        for method in (wl.CFD, wl.MFD):
+            sp = wl.seismic_spec(method, side, side, 4, h=5.0, seed=5)
+            s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32)
+            s.set_source(*sp.source.as_tuple())
+            chosen, ms = s.autotune(trials=4, force=True)
+            cap, ring = s.launch()
+            s.step(8)  # graph capture of the 8-step loop
+            s.sync()
+            t0 = time.perf_counter()
+            s.step(8)
+            s.sync()
+            tuned = 1e3 * (time.perf_counter() - t0) / 8
+            s.close()
+            out["%s_%d" % (wl.METHOD_NAMES[method], side)] = {
+                "ms_per_step": {names[k]: v for k, v in ms.items()}, "chosen": names[chosen],
+                "lines_per_cta_cap": cap, "ring_cap": ring, "tuned_wall_ms_per_step": tuned}
+    return out
+
+
+def batch256_leg(adi, torch, peak, steps=100):
+    """Config 3: 256 independent simulations (128 CFD + 128 MFD), sides uniform in [128, 1024],
+    seeded layered media, Ricker sources, FP32, batched.  `steps` graph-captured steps after
+    warm-up, CUDA events on the batch's stream; then a few half-step pairs with events around
+    the solve launches for the kernels' roofline (20 B per point and stage)."""
+    from paper_2006_07583_gb300 import workloads as wl
+
+    specs = wl.batch_specs(256, 128, 1024, steps, seed=2)
+    sims = []
+    for sp in specs:
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32)
+        s.set_source(*sp.source.as_tuple())
+        sims.append(s)
+    b = adi.Batch(sims)
+    stream = torch.cuda.Stream()
+    b.set_stream(stream.cuda_stream)
+    b.step(steps)  # graph capture and warm-up
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    b.set_timing(True)
+    for _ in range(10):
+        b.half_step(1)
+        b.half_step(2)
+    solve = [b.solve_time(st) for st in (1, 2)]
+    solve_ms = max(t / max(n, 1) for t, n in solve)
+    pts = sum(sp.nx * sp.ny for sp in specs)
+    achieved = 5 * 4 * pts / (solve_ms / 1e3) / 1e9
+    b.close()
+    for s in sims:
+        s.close()
+    return {"workload": "config 3: 256 sims (128 CFD + 128 MFD), sides uniform 128-1024, FP32, "
+                        "one batch, graph-captured steps", "value": pts / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "points": pts,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "solve_ms": solve_ms}}
+
+
+def fp64_factored_leg(adi, torch, side, peak, steps=4):
+    """The default (factored) solver in FP64 on the bench's two 4096^2 simulations, batched:
+    updates/s, the solve kernels' fraction of HBM (40 B per point and stage in FP64), and the
+    device's measured FP64 and FP32 FMA throughput (adi_fma_peak) for the ALU roofline."""
+    specs = make_specs(side, steps)
+    sims = []
+    for sp in specs:
+        s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP64)
+        s.set_source(*sp.source.as_tuple())
+        sims.append(s)
+    b = adi.Batch(sims)
+    stream = torch.cuda.Stream()
+    b.set_stream(stream.cuda_stream)
+    b.half_step(1)
+    b.half_step(2)
+    stream.synchronize()
+    b.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            b.half_step(1)
+            b.half_step(2)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    solve = [b.solve_time(st) for st in (1, 2)]
+    solve_ms = max(t / max(n, 1) for t, n in solve)
+    pts = sum(sp.nx * sp.ny for sp in specs)
+    solver = {0: "line", 1: "chunked", 2: "factored"}[sims[0].solver]
+    b.close()
+    for s in sims:
+        s.close()
+    hbm = 5 * 8 * pts / (solve_ms / 1e3) / 1e9
+    return {"workload": "batched FP64 PR-ADI, 1 CFD + 1 MFD seismic sim at %dx%d cells" % (side, side),
+            "value": pts / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "solver": solver,
+            "solve_ms": solve_ms, "hbm_frac": hbm / peak, "hbm_achieved_gbs": hbm,
+            "fma_peak_tflops": {"fp64": adi.fma_peak(adi.ADI_FP64) / 1e12,
+                                "fp32": adi.fma_peak(adi.ADI_FP32) / 1e12}}
 
 
 def fp64_plain(adi, side):

@@ -121,6 +121,20 @@ int adi_get_solver(adi_handle sim);
  */
 int adi_autotune(adi_handle sim, int trials, int force, int *chosen, double *ms_per_step);
 
+/*
+ * adi_set_launch / adi_get_launch -- launch parameters of the factored line solver (the paper
+ * has no counterpart: GPU launch shape).  lines_per_cta caps the lines one CTA solves together
+ * (0: as many as its threads and shared memory take); ring_depth caps the staged groups in
+ * flight per CTA (2 or 0: prefetch the next group while solving one, 1: no prefetch).  The
+ * results do not change (every line is solved by the same arithmetic), only the time.  When
+ * the factored solver is the fastest, adi_autotune also times every lines_per_cta from the
+ * automatic count halved down to 1 with both ring depths, keeps the fastest and caches it with
+ * the solver choice; adi_get_launch reports the current caps (0 = automatic).
+ * Errors: ADI_EINVAL, ADI_EBUSY inside a batch.
+ */
+int adi_set_launch(adi_handle sim, int lines_per_cta, int ring_depth);
+int adi_get_launch(adi_handle sim, int *lines_per_cta, int *ring_depth);
+
 /* Device bytes adi_create allocates for this configuration with its default solver (0 if
  * invalid); transient staging buffers are not included. */
 size_t adi_state_bytes(int method, int nx, int ny, int precision);
@@ -157,6 +171,23 @@ int adi_set_source(adi_handle sim, int is, int js, double amp, double f0, double
  */
 int adi_set_harmonic(adi_handle sim, const double *B, const double *F, double omega,
                      double phase_b, double phase_f);
+
+/*
+ * adi_set_sponge -- absorbing layers along every wall: Cerjan's damping, the technique Sec. 2.1
+ * names for absorbing boundaries.  After every full step each field value at a point whose
+ * distance to the nearest wall is delta cells, delta < width, is multiplied by
+ *     g = exp(-(a (width - delta))^2)
+ * (Cerjan's classic choice is width 20, a = 0.015); the pressure's wall values (the Dirichlet
+ * data) are not damped.  Distances use the mesh of each field: nodes (CFD), cell centres and
+ * faces (MFD).  width = 0 or a = 0 removes the layers.
+ * A simulation with layers writes its natural fields every step and rebuilds its carried state
+ * from the damped fields (the work of adi_set_fields' prologue), about one more stage's worth
+ * of memory traffic per step.  Works with batches, graphs, sources and adi_set_harmonic.
+ * Device memory: the y-line descriptors of both parities and the prologue's scratch.
+ * Errors: ADI_EINVAL (negative or non-finite values), ADI_EBUSY in a batch, ADI_ENOMEM,
+ * ADI_ECUDA.
+ */
+int adi_set_sponge(adi_handle sim, double width, double a);
 
 /* adi_set_stream -- CUDA stream (cudaStream_t, NULL = legacy default) for later calls. */
 int adi_set_stream(adi_handle sim, void *cuda_stream);

@@ -63,6 +63,9 @@ _SIGS = {
                          ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp], ctypes.c_int),
     "adi_set_harmonic": ([_vp, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
     "adi_fma_peak": ([ctypes.c_int, _dp], ctypes.c_int),
+    "adi_set_sponge": ([_vp, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "adi_set_launch": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "adi_get_launch": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "adi_step": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_sync": ([_vp], ctypes.c_int),
     "adi_read_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
@@ -235,6 +238,11 @@ class Sim:
         _check(lib().adi_set_harmonic(self._h, bp, fp, float(omega), float(phase_b), float(phase_f)),
                "adi_set_harmonic")
 
+    def set_sponge(self, width, a):
+        """adi_set_sponge: Cerjan absorbing layers `width` cells wide with strength `a`
+        (width 0 or a 0 removes them)."""
+        _check(lib().adi_set_sponge(self._h, float(width), float(a)), "adi_set_sponge")
+
     def set_stream(self, stream_ptr):
         _check(lib().adi_set_stream(self._h, _vp(stream_ptr)), "adi_set_stream")
 
@@ -253,6 +261,16 @@ class Sim:
         _check(lib().adi_autotune(self._h, int(trials), 1 if force else 0, ctypes.byref(chosen), ms),
                "adi_autotune")
         return chosen.value, {k: ms[k] for k in range(3) if ms[k] >= 0}
+
+    def set_launch(self, lines_per_cta=0, ring_depth=0):
+        """adi_set_launch: the factored solver's lines per CTA and staging ring depth (0 = auto)."""
+        _check(lib().adi_set_launch(self._h, int(lines_per_cta), int(ring_depth)), "adi_set_launch")
+
+    def launch(self):
+        """adi_get_launch: (lines_per_cta cap, ring depth cap), 0 = automatic."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().adi_get_launch(self._h, ctypes.byref(a), ctypes.byref(b)), "adi_get_launch")
+        return a.value, b.value
 
     def step(self, n=1):
         _check(lib().adi_step(self._h, int(n)), "adi_step")

@@ -188,6 +188,7 @@ struct Plan {
     int fstages[2][kFacVariants] = {};    // pipeline depth (2 = prefetch)
     int fgrid[2][kFacVariants] = {};      // persistent CTAs
     int freach[2][kFacVariants] = {};     // largest scan reach of the launch's lines
+    int fring[2][kFacVariants] = {};      // ring-depth cap of the launch (0: none)
     // carried-pressure transposes after each stage, one array per member: [dir]
     DevBuf tdesc[2];
     int tcount[2] = {0, 0}, trows[2] = {0, 0}, tcols[2] = {0, 0};
@@ -196,6 +197,19 @@ struct Plan {
     DevBuf hdesc;
     int hcount = 0;
     size_t hmax = 0;
+    // absorbing layers: per member with layers, what runs after its stage 2 (per plan parity q)
+    struct SpongeStep {
+        SpongeRec rec[2];         // the natural fields to damp (v: the copy stage 1 wrote)
+        const void *ydesc[2];     // y-line descriptors of the next step's parity
+        int nlines = 0, N = 0, method = 0;
+        void *scr = nullptr;      // prologue scratch, then (CFD) the Thomas factors
+        const void *fac = nullptr;
+        long long st = 1;
+        void *A3 = nullptr, *A0 = nullptr;
+        int rows_u = 0, ldu = 0, ldc = 0, lda = 0;
+        int harm = -1;            // index of the member's harmonic record, or -1
+    };
+    std::vector<SpongeStep> sponges;
     std::map<int, cudaGraphExec_t> graphs;
 };
 
@@ -216,6 +230,7 @@ void plan_free(Plan &p) {
             p.fstages[d][v] = 0;
             p.fgrid[d][v] = 0;
             p.freach[d][v] = 0;
+            p.fring[d][v] = 0;
         }
         p.v1n[d] = 0;
         p.ngroups[d][0] = p.ngroups[d][1] = 0;
@@ -230,6 +245,7 @@ void plan_free(Plan &p) {
     dev_free(p.hdesc);
     p.hcount = 0;
     p.hmax = 0;
+    p.sponges.clear();
 }
 
 // ADI_ETIMEOUT if a launch of the plan gave up waiting for its staged inputs.
@@ -260,6 +276,9 @@ struct adi_sim {
     int nlines[2] = {0, 0};
     int solver = ADI_SOLVER_CHUNKED;
     int fac_reach = 0;                        // largest scan reach of the factored records
+    // factored solver's launch parameters (0 = automatic): at most fac_nl_cap lines per CTA,
+    // fac_ring_cap staged groups in flight (1: no prefetch); chosen by adi_autotune
+    int fac_nl_cap = 0, fac_ring_cap = 0;
     Plan plan;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -275,6 +294,12 @@ struct adi_sim {
     bool harm_on = false;
     double h_omega = 0, h_phb = 0, h_phf = 0;
     DevBuf h_edges, h_frow, h_fcol, h_self;
+    // absorbing layers (adi_set_sponge): width in cells and strength; the y-line descriptors
+    // of both parities and the prologue's scratch (with the CFD Thomas factors) kept on the
+    // device for the per-step rebuild of the carried state
+    bool sp_on = false;
+    double sp_width = 0, sp_a = 0;
+    DevBuf sp_desc[2], sp_scr;
 };
 
 struct adi_batch_t {
@@ -555,6 +580,7 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                     }
                 } else {
                     int nl = fac_lines_per_cta(s->g.method, N, esz);
+                    if (s->fac_nl_cap > 0) nl = std::min(nl, s->fac_nl_cap);
                     for (int st = 0; st < n; st += nl) {
                         int cnt = std::min(nl, n - st);
                         fgr[dir][v].push_back(fac_group_of(s->g.method, N, first + st, cnt, 1.0 / s->h, 0.5 * s->dt));
@@ -562,6 +588,8 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                     }
                 }
                 p.freach[dir][v] = std::max(p.freach[dir][v], s->fac_reach);
+                if (s->fac_ring_cap > 0)
+                    p.fring[dir][v] = p.fring[dir][v] > 0 ? std::min(p.fring[dir][v], s->fac_ring_cap) : s->fac_ring_cap;
                 for (int q = 0; q < 2; ++q) {
                     const std::vector<unsigned char> &h = s->h_desc[s->parity ^ q][dir];
                     fdv[q][dir].insert(fdv[q][dir].end(), h.begin(), h.end());
@@ -612,6 +640,7 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
         for (int v = 0; v < kFacVariants && !rc; ++v) {
             p.nfgroups[dir][v] = (int)fgr[dir][v].size();
             p.fstages[dir][v] = fac_stages_for(p.fstage[dir][v], esz);
+            if (p.fring[dir][v] > 0) p.fstages[dir][v] = std::min(p.fstages[dir][v], p.fring[dir][v]);
             p.fgrid[dir][v] = std::min(p.nfgroups[dir][v], sm_count());
             if (p.nfgroups[dir][v] && !p.fstages[dir][v]) { rc = ADI_ENOTSUP; break; }
             if (!fgr[dir][v].empty()) {
@@ -664,6 +693,35 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                                                       cudaMemcpyHostToDevice, stream));
         }
     }
+    // the absorbing layers' per-step work, with each such member's own descriptor copies
+    int hidx = 0;
+    for (adi_sim *s : members) {
+        const int my_h = s->harm_on ? hidx++ : -1;
+        if (!s->sp_on || rc) continue;
+        const Geometry &g = s->g;
+        for (int par = 0; par < 2 && !rc; ++par)
+            rc = cuda_status(cudaMemcpyAsync(s->sp_desc[par].p, s->h_desc[par][1].data(), s->h_desc[par][1].size(),
+                                             cudaMemcpyHostToDevice, stream));
+        Plan::SpongeStep sp;
+        for (int q = 0; q < 2; ++q) {
+            const int pm = s->parity ^ q;  // the member's parity at plan parity q
+            SpongeRec &r = sp.rec[q];
+            r.uo = s->Uo.p; r.v = s->V[1 - pm].p; r.wo = s->Wo.p; r.v_other = s->V[pm].p;
+            r.method = g.method; r.nx = g.nx; r.ny = g.ny;
+            r.rows_u = g.rows_u; r.ldu = g.ldu; r.rows_v = g.rows_v; r.ldv = g.ldv; r.ldvp = g.ldvp;
+            r.rows_w = g.rows_w; r.ldw = g.ldw;
+            r.width = s->sp_width; r.a = s->sp_a;
+            sp.ydesc[q] = s->sp_desc[1 - pm].p;
+        }
+        sp.nlines = s->nlines[1]; sp.N = g.ny; sp.method = g.method;
+        sp.st = std::max(1, s->nlines[1]);
+        sp.scr = s->sp_scr.p;
+        sp.fac = g.method == ADI_CFD ? (const void *)((unsigned char *)s->sp_scr.p + (size_t)(2 * g.ny + 2) * sp.st * s->esz) : nullptr;
+        sp.A3 = s->A[3].p; sp.A0 = s->A[0].p;
+        sp.rows_u = g.rows_u; sp.ldu = g.ldu; sp.ldc = g.ldc; sp.lda = g.lda;
+        sp.harm = my_h;
+        p.sponges.push_back(sp);
+    }
     if (!rc) rc = dev_alloc(p.fault, sizeof(int));
     if (!rc) rc = cuda_status(cudaMemsetAsync(p.fault.p, 0, sizeof(int), stream));
     if (!rc && (p.v1n[0] || p.v1n[1])) {
@@ -681,7 +739,8 @@ template <typename T>
 cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream_t stream, cudaEvent_t ev0,
                           cudaEvent_t ev1) {
     cudaError_t e = ev0 ? cudaEventRecord(ev0, stream) : cudaSuccess;
-    int nat = dir == 1 ? natural : 0;
+    // members with absorbing layers need their natural fields after every step
+    int nat = dir == 1 ? (natural || !p.sponges.empty() ? 1 : 0) : 0;
     if (e == cudaSuccess && p.v1n[dir])
         e = launch_line_solve_v1<T>((const LineDesc<T> *)p.v1d[q][dir].p, p.v1n[dir], (T *)p.scratch.p,
                                     p.scratch_stride, nat, stream);
@@ -710,6 +769,23 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
     // time-harmonic walls and forcing, in the layout the next stage reads
     if (e == cudaSuccess && p.hcount)
         e = launch_harmonic<T>((const HarmDesc *)p.hdesc.p, p.hcount, p.hmax, dir, stream);
+    // absorbing layers: damp the natural fields, rebuild the carried state from them
+    if (dir == 1)
+        for (const Plan::SpongeStep &sp : p.sponges) {
+            if (e != cudaSuccess) break;
+            e = launch_sponge<T>(sp.rec[q], stream);
+            if (e == cudaSuccess)
+                e = launch_prologue_lines<T>((const LineDesc<T> *)sp.ydesc[q], sp.nlines, sp.N, sp.method,
+                                             (const T *)sp.fac, (T *)sp.scr, sp.st, stream);
+            if (e == cudaSuccess) {  // the prologue wrote a column-major (A[3]); a row-major copy
+                dim3 grid((unsigned)((sp.rows_u + 31) / 32), (unsigned)((sp.ldu + 31) / 32)), block(32, 8);
+                transpose_kernel<T><<<grid, block, 0, stream>>>((const T *)sp.A3, sp.ldu, sp.rows_u, sp.ldc,
+                                                                (T *)sp.A0, sp.lda);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess && sp.harm >= 0)
+                e = launch_harmonic<T>((const HarmDesc *)p.hdesc.p + sp.harm, 1, (size_t)sp.rows_u * sp.ldu, 3, stream);
+        }
     return e;
 }
 
@@ -778,7 +854,7 @@ int run_prologue_t(adi_sim *s) {
     const LineDesc<T> *cols = (const LineDesc<T> *)((unsigned char *)s->cold_all.p + s->h_desc[s->parity][0].size());
     const long long st = std::max(1, s->nlines[1]);
     const int N = s->g.ny;
-    const size_t scr = (size_t)(2 * N + 2) * st, nfac = s->g.method == ADI_CFD ? (size_t)6 * N : 0;
+    const size_t scr = (size_t)(2 * N + 2) * st, nfac = s->g.method == ADI_CFD ? prologue_factor_count(N) : 0;
     const size_t bytes = (scr + nfac) * sizeof(T);
     cudaError_t e = cudaSuccess;
     if (s->pro.bytes != bytes) {  // first use: scratch plus the CFD Thomas factors of P, Pbar
@@ -1106,6 +1182,8 @@ namespace {
 struct TuneResult {
     int solver = ADI_SOLVER_LINE;
     double ms[3] = {-1.0, -1.0, -1.0};
+    int nl_cap = 0, ring_cap = 0;  // the factored solver's launch parameters (0 = automatic)
+    double ms_launch = -1.0;       // time per step with them
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, TuneResult> g_tune;
@@ -1184,6 +1262,8 @@ int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_pe
         if (rc) { dev_free(snap); return rc == ADI_ENOMEM ? ADI_ENOMEM : (s->sticky = rc); }
         const int parity0 = s->parity, solver0 = s->solver;
         const long long steps0 = s->steps;
+        s->fac_nl_cap = 0;  // the solvers are compared with the automatic launch parameters
+        s->fac_ring_cap = 0;
         const int n = trials + (trials & 1);  // even: both runs start at the same parity
         double best = 0.0;
         res.solver = -1;
@@ -1204,6 +1284,31 @@ int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_pe
             res.ms[sv] = ms;
             if (res.solver < 0 || ms < best) { best = ms; res.solver = sv; }
         }
+        // the factored solver's launch parameters: lines per CTA (the automatic count, then
+        // halved down to one) and the staging ring depth (2: prefetch, 1: none)
+        if (!rc && res.solver == ADI_SOLVER_FACTORED) {
+            rc = adi_set_solver(s, ADI_SOLVER_FACTORED);
+            const int nl0 = std::max(fac_split_line(s->g.method, s->g.nx) ? 1 : fac_lines_per_cta(s->g.method, s->g.nx, s->esz),
+                                     fac_split_line(s->g.method, s->g.ny) ? 1 : fac_lines_per_cta(s->g.method, s->g.ny, s->esz));
+            std::vector<int> caps = {0};
+            for (int c = nl0 / 2; c >= 1; c /= 2) caps.push_back(c);
+            res.ms_launch = res.ms[ADI_SOLVER_FACTORED];
+            for (size_t ci = 0; ci < caps.size() && !rc; ++ci)
+                for (int ring = 0; ring <= 1 && !rc; ++ring) {
+                    if (ci == 0 && ring == 0) continue;  // the automatic choice, timed above
+                    s->fac_nl_cap = caps[ci];
+                    s->fac_ring_cap = ring;
+                    rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
+                    s->plan_base = s->parity;
+                    double ms = 0.0;
+                    if (!rc) rc = time_steps(s, n, &ms);
+                    if (!rc) rc = copy_state(s, snap, false);
+                    if (rc) break;
+                    s->parity = parity0;
+                    s->steps = steps0;
+                    if (ms < res.ms_launch) { res.ms_launch = ms; res.nl_cap = caps[ci]; res.ring_cap = ring; }
+                }
+        }
         if (rc) {
             dev_free(snap);
             return s->sticky = rc;
@@ -1213,11 +1318,34 @@ int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_pe
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = res;
     }
-    rc = adi_set_solver(s, res.solver);
+    s->fac_nl_cap = res.solver == ADI_SOLVER_FACTORED ? res.nl_cap : 0;
+    s->fac_ring_cap = res.solver == ADI_SOLVER_FACTORED ? res.ring_cap : 0;
+    rc = adi_set_solver(s, res.solver);  // rebuilds the plan with the chosen parameters
     if (rc) return rc;
     if (chosen) *chosen = res.solver;
     if (ms_per_step)
         for (int k = 0; k < 3; ++k) ms_per_step[k] = res.ms[k];
+    return ADI_OK;
+}
+
+int adi_set_launch(adi_handle s, int lines_per_cta, int ring_depth) {
+    if (!s || lines_per_cta < 0 || ring_depth < 0 || ring_depth > 2) return ADI_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (s->in_batch) return ADI_EBUSY;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->sticky = cuda_status(e);
+    s->fac_nl_cap = lines_per_cta;
+    s->fac_ring_cap = ring_depth == 2 ? 0 : ring_depth;
+    int rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
+    s->plan_base = s->parity;
+    if (rc) s->sticky = rc;
+    return rc;
+}
+
+int adi_get_launch(adi_handle s, int *lines_per_cta, int *ring_depth) {
+    if (!s) return ADI_EINVAL;
+    if (lines_per_cta) *lines_per_cta = s->fac_nl_cap;
+    if (ring_depth) *ring_depth = s->fac_ring_cap;
     return ADI_OK;
 }
 
@@ -1281,6 +1409,55 @@ int adi_set_harmonic(adi_handle s, const double *B, const double *F, double omeg
     if (!rc) rc = load_state(s, nullptr, nullptr, nullptr, true);
     dev_free(s->xfer);
     dev_free(s->pro);
+    if (rc) s->sticky = rc;
+    return rc;
+}
+
+int adi_set_sponge(adi_handle s, double width, double a) {
+    if (!s) return ADI_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (s->in_batch) return ADI_EBUSY;
+    if (!std::isfinite(width) || !std::isfinite(a) || width < 0 || a < 0) return ADI_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->sticky = cuda_status(e);
+    int rc = ADI_OK;
+    if (width == 0 || a == 0) {
+        if (!s->sp_on) return ADI_OK;
+        s->sp_on = false;
+        dev_free(s->sp_desc[0]); dev_free(s->sp_desc[1]); dev_free(s->sp_scr);
+    } else {
+        const Geometry &g = s->g;
+        const long long st = std::max(1, s->nlines[1]);
+        const int N = g.ny;
+        const size_t scr = (size_t)(2 * N + 2) * st, nfac = g.method == ADI_CFD ? prologue_factor_count(N) : 0;
+        const size_t dbytes = s->h_desc[0][1].size();
+        if (s->sp_desc[0].bytes != dbytes) {
+            dev_free(s->sp_desc[0]); dev_free(s->sp_desc[1]);
+            rc = dev_alloc(s->sp_desc[0], dbytes);
+            if (!rc) rc = dev_alloc(s->sp_desc[1], dbytes);
+        }
+        if (!rc && s->sp_scr.bytes != (scr + nfac) * s->esz) {
+            dev_free(s->sp_scr);
+            rc = dev_alloc(s->sp_scr, (scr + nfac) * s->esz);
+            if (!rc && nfac) {
+                std::vector<double> f;
+                prologue_factors(N, f);
+                if (s->precision == ADI_FP64) {
+                    rc = cuda_status(cudaMemcpyAsync((double *)s->sp_scr.p + scr, f.data(), f.size() * sizeof(double),
+                                                     cudaMemcpyHostToDevice, s->stream));
+                    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));
+                } else {
+                    std::vector<float> ff(f.begin(), f.end());
+                    rc = cuda_status(cudaMemcpyAsync((float *)s->sp_scr.p + scr, ff.data(), ff.size() * sizeof(float),
+                                                     cudaMemcpyHostToDevice, s->stream));
+                    if (!rc) rc = cuda_status(cudaStreamSynchronize(s->stream));  // ff leaves scope
+                }
+            }
+        }
+        if (!rc) { s->sp_on = true; s->sp_width = width; s->sp_a = a; }
+    }
+    if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
+    s->plan_base = s->parity;
     if (rc) s->sticky = rc;
     return rc;
 }
@@ -1423,7 +1600,8 @@ int adi_destroy(adi_handle s) {
     plan_free(s->plan);
     DevBuf *bufs[] = {&s->A[0], &s->A[1], &s->A[2], &s->A[3], &s->V[0], &s->V[1], &s->W[0], &s->W[1], &s->alpha,
                       &s->alphaT, &s->Uo, &s->Wo, &s->tab, &s->sep, &s->cold_all, &s->clock, &s->status,
-                      &s->xfer, &s->pro, &s->h_edges, &s->h_frow, &s->h_fcol, &s->h_self};
+                      &s->xfer, &s->pro, &s->h_edges, &s->h_frow, &s->h_fcol, &s->h_self,
+                      &s->sp_desc[0], &s->sp_desc[1], &s->sp_scr};
     for (DevBuf *b : bufs) dev_free(*b);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     (void)cudaGetLastError();

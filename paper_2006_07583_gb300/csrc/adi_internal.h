@@ -57,7 +57,10 @@ cudaError_t launch_line_solve_v1(const LineDesc<T> *d, int nlines, T *scratch,
 template <typename T>
 cudaError_t launch_prologue(const LineDesc<T> *col_lines, int nlines, const T *fac, T *scratch,
                             long long scratch_stride, cudaStream_t s);
-void prologue_factors(int N, std::vector<double> &out);  // CFD: 3 (N+1) + 3 (N-1) values
+// CFD: 3 (N+1) + 3 (N-1) Thomas factors of P and Pbar, then the start-up factors of the
+// chunked solves (prologue_factor_count(N) values in all)
+void prologue_factors(int N, std::vector<double> &out);
+size_t prologue_factor_count(int N);
 // The prologue over the y-lines of one simulation (N cells each) with one thread per line
 // element for the stencils (and, for CFD, one per line for the Thomas solves with fac).
 // scratch: 2N elements per line (element k at k * st + line).
@@ -87,6 +90,19 @@ struct HarmDesc {
 // clock's time; 3: the carried state after a prologue.  max_points: the largest rows_u * ldu.
 template <typename T>
 cudaError_t launch_harmonic(const HarmDesc *d, int n, size_t max_points, int mode, cudaStream_t s);
+
+// Absorbing layers (adi_sponge.cu): the damped fields of one simulation after a step.
+struct SpongeRec {
+    void *uo, *v, *wo;          // natural u (rows_u x ldu), natural v (rows_v x ldv, leading
+                                // dimension ldvp), natural w (rows_w x ldw)
+    void *v_other;              // the other copy of v: its first and last rows, which no x-line
+                                // writes, must hold the same damped values
+    int method, nx, ny;
+    int rows_u, ldu, rows_v, ldv, ldvp, rows_w, ldw;
+    double width, a;            // layer width in cells, damping strength
+};
+template <typename T>
+cudaError_t launch_sponge(const SpongeRec &r, cudaStream_t s);
 
 // Factored solver (adi_factored.cu).
 // One line group of a launch, built on the host: lines [first, first + nl) of one simulation

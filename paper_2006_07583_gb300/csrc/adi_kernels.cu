@@ -378,12 +378,11 @@ __global__ void prologue_kernel(const LineDesc<T> *__restrict__ descs, int nline
 }
 
 // ---------------------------------------------------------------------------------------
-// The same prologue with one thread per (line, element) for everything but the CFD Thomas
-// solves.  prologue_stencil_kernel: block (32 lines, 8 elements); for CFD it leaves
-// (Q u)_j / h (j = 0..N) and (Qbar w)_j / h (j = 1..N-1) in the scratch (element k of a line
-// at k * st + line), for MFD it writes w* and a directly.  prologue_solve_kernel (CFD, one
-// thread per line): the two Thomas solves with the precomputed factors, each output written
-// as its back-substitution produces it.
+// The same prologue spread over the lines' elements.  prologue_stencil_kernel: block (32
+// lines, 8 elements); for CFD it leaves (Q u)_j / h (j = 0..N) and (Qbar w)_j / h (j = 1..N-1)
+// in the scratch (element k of a line at k * st + line), for MFD it writes w* and a directly.
+// prologue_solve_win_kernel (CFD): the two Thomas solves with the precomputed factors, one
+// thread per chunk of a line (below).
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T prologue_src(const LineDesc<T> &d) {
@@ -435,62 +434,92 @@ __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, i
     }
 }
 
+// The same two Thomas solves spread over chunks of kProR rows of every line, one thread per
+// (line, chunk): a line of 4097 rows gives 65 threads instead of one, so the solve is no longer a
+// chain of thousands of dependent steps per thread.  Each thread solves the rows of its chunk
+// plus a halo of kProH rows on each side that are not at a line end, with the values beyond the
+// halo taken as zero.  Away from the two boundary rows P and Pbar are tridiag(1, 4, 1), whose
+// inverse decays by a factor 2 - sqrt(3) = 0.268 per row, so what the truncation leaves out is
+// 0.268^32 = 5e-19 of the solution: the result equals the whole-line solve to rounding.  A
+// window that starts inside the line eliminates from its first row as if it had no
+// predecessor; those rows are interior rows, and the start-up factors of that elimination (the
+// last kProH values of the factor buffer) join the whole line's factors within kProH rows.
+constexpr int kProR = 64, kProH = 32;
+
+template <typename T, typename Out>
+__host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r1, const T *q, long long st,
+                                                   const T *lo, const T *cu, const T *id, const T *su_id,
+                                                   T *tmp, long long ts, Out out) {
+    const int s = r0 > 0 ? r0 - kProH : 0;
+    const int e = r1 + kProH < n ? r1 + kProH : n;
+    T dd = T(0);
+    for (int r = s; r < r0; ++r) dd = (q[(long long)r * st] - dd) * su_id[r - s];  // start-up rows
+    for (int r = r0; r < r1; ++r) {
+        dd = (q[(long long)r * st] - lo[r] * dd) * id[r];
+        tmp[(long long)r * ts] = dd;
+    }
+    T hh[kProH];
+#pragma unroll
+    for (int k = 0; k < kProH; ++k) {
+        const int r = r1 + k;
+        if (r < e) {
+            dd = (q[(long long)r * st] - lo[r] * dd) * id[r];
+            hh[k] = dd;
+        }
+    }
+    T x = T(0);
+#pragma unroll
+    for (int k = kProH - 1; k >= 0; --k) {
+        const int r = r1 + k;
+        if (r < e) x = hh[k] - cu[r] * x;
+    }
+    for (int r = r1 - 1; r >= r0; --r) {
+        x = tmp[(long long)r * ts] - cu[r] * x;
+        out(r, x);
+    }
+}
+
+// grid.y: the chunks of P (N+1 rows) first, then those of Pbar (N-1 rows).
 template <typename T>
-__global__ void prologue_solve_kernel(const LineDesc<T> *__restrict__ descs, int nlines, int N, const T *scratch,
-                                      long long st, const T *__restrict__ fac) {
+__global__ void prologue_solve_win_kernel(const LineDesc<T> *__restrict__ descs, int nlines, int N, const T *scratch,
+                                          long long st, const T *__restrict__ fac) {
     const int line = blockIdx.x * blockDim.x + threadIdx.x;
     if (line >= nlines) return;
     const LineDesc<T> &d = descs[line];
     const T beta = (T)d.beta;
     const T *un = d.u_out, *wn = d.w_out;
     const long long snp = d.snp, snv = d.snv, spo = d.spo;
-    T *q = (T *)scratch + line;
-    // P g = (Q u)/h over rows 0..N; w*_j = w_j - beta g_j
-    {
+    const int nP = N + 1, nB = N - 1;
+    const int chP = (nP + kProR - 1) / kProR;
+    const T *su_id = fac + 3 * (N + 1) + 3 * (N - 1);
+    const T *q = scratch + line;
+    if ((int)blockIdx.y < chP) {
+        // P g = (Q u)/h over rows 0..N; w*_r = w_r - beta g_r
+        const int r0 = blockIdx.y * kProR, r1 = min(nP, r0 + kProR);
         const T *lo = fac, *cu = fac + (N + 1), *id = fac + 2 * (N + 1);
-        T dd = q[0] * id[0];
-        q[0] = dd;
-#pragma unroll 4
-        for (int r = 1; r <= N; ++r) {
-            dd = (q[(long long)r * st] - lo[r] * dd) * id[r];
-            q[(long long)r * st] = dd;
-        }
-        T x = dd;
-        d.v[(long long)N * d.sv] = wn[(long long)N * snv] - beta * x;
-#pragma unroll 4
-        for (int r = N - 1; r >= 0; --r) {
-            x = q[(long long)r * st] - cu[r] * x;
-            d.v[(long long)r * d.sv] = wn[(long long)r * snv] - beta * x;
-        }
-    }
-    // Pbar e = (Qbar w)/h over nodes 1..N-1 (rows 0..N-2); a_j = u_j - alpha_j e_j (+ source)
-    {
+        T *v = d.v;
+        const long long sv = d.sv;
+        prologue_win_solve<T>(nP, r0, r1, q, st, lo, cu, id, su_id, v, sv,
+                              [&](int r, T g) { v[(long long)r * sv] = wn[(long long)r * snv] - beta * g; });
+    } else {
+        // Pbar e = (Qbar w)/h over nodes 1..N-1 (rows 0..N-2); a_j = u_j - alpha_j e_j (+ source)
+        const int c = blockIdx.y - chP;
+        const int r0 = c * kProR, r1 = min(nB, r0 + kProR);
         const T *fb = fac + 3 * (N + 1);
         const T *lo = fb, *cu = fb + (N - 1), *id = fb + 2 * (N - 1);
-        T *qb = q + (long long)(N + 1) * st;  // element r = node r + 1
-        T dd = qb[0] * id[0];
-        qb[0] = dd;
-#pragma unroll 4
-        for (int r = 1; r < N - 1; ++r) {
-            dd = (qb[(long long)r * st] - lo[r] * dd) * id[r];
-            qb[(long long)r * st] = dd;
-        }
+        const T *qb = q + (long long)(N + 1) * st;
         const T src = d.src_k >= 0 ? prologue_src(d) : T(0);
-        T x = dd;
-        auto out = [&](int r, T e) {
+        T *po = d.po;
+        prologue_win_solve<T>(nB, r0, r1, qb, st, lo, cu, id, su_id, po + spo, spo, [&](int r, T e) {
             const int j = r + 1;
             T val = un[(long long)j * snp] - d.alpha[(long long)j * d.sp] * e;
             if (j == d.src_k) val += src;
-            d.po[(long long)j * spo] = val;
-        };
-        out(N - 2, x);
-#pragma unroll 4
-        for (int r = N - 3; r >= 0; --r) {
-            x = qb[(long long)r * st] - cu[r] * x;
-            out(r, x);
+            po[(long long)j * spo] = val;
+        });
+        if (c == 0) {
+            po[0] = un[0];
+            po[(long long)N * spo] = un[(long long)N * snp];
         }
-        d.po[0] = un[0];
-        d.po[(long long)N * spo] = un[(long long)N * snp];
     }
 }
 
@@ -538,16 +567,29 @@ cudaError_t launch_prologue_lines(const LineDesc<T> *d, int nlines, int N, int m
     if (nlines <= 0) return cudaSuccess;
     dim3 grid((unsigned)((nlines + 31) / 32), (unsigned)((N + 2 + 7) / 8));
     prologue_stencil_kernel<T><<<grid, dim3(32, 8), 0, s>>>(d, nlines, N, method, scratch, st);
-    if (method == kCFD)
-        prologue_solve_kernel<T><<<(nlines + 127) / 128, 128, 0, s>>>(d, nlines, N, scratch, st, fac);
+    if (method == kCFD) {
+        const unsigned chunks = (unsigned)((N + 1 + kProR - 1) / kProR + (N - 1 + kProR - 1) / kProR);
+        prologue_solve_win_kernel<T><<<dim3((unsigned)((nlines + 127) / 128), chunks), 128, 0, s>>>(d, nlines, N,
+                                                                                                 scratch, st, fac);
+    }
     return cudaGetLastError();
 }
 
 // Thomas factors of the App. A P (N+1 rows) and Pbar (N-1 rows), for the prologue: per matrix
 // the sub-diagonal, the eliminated super-diagonal c_r = up_r / den_r and 1 / den_r, where
 // den_r = di_r - lo_r c_{r-1}; built in FP64.
+size_t prologue_factor_count(int N) { return (size_t)3 * (N + 1) + 3 * (N - 1) + kProH; }
 void prologue_factors(int N, std::vector<double> &out) {
-    out.assign(3 * (N + 1) + 3 * (N - 1), 0.0);
+    out.assign(prologue_factor_count(N), 0.0);
+    // start-up factors of a window that begins on an interior row (no predecessor): 1 / den_k with
+    // den_0 = 4, den_k = 4 - 1 / den_{k-1}
+    {
+        double *su = out.data() + 3 * (N + 1) + 3 * (N - 1), den = 4.0;
+        for (int k = 0; k < kProH; ++k) {
+            su[k] = 1.0 / den;
+            den = 4.0 - su[k];
+        }
+    }
     for (int bar = 0; bar < 2; ++bar) {
         const int n = bar ? N - 1 : N + 1;
         double *lo = out.data() + (bar ? 3 * (N + 1) : 0), *cu = lo + n, *id = cu + n;

@@ -1,9 +1,12 @@
 // Host-only check of the prologue's Thomas factors (prologue_factors): for several line
-// lengths, P x = b and Pbar x = b solved with the stored factors (the elimination the kernel
-// runs) agree with a dense Gaussian elimination of the same App. A matrices, assembled from
-// their row functions.  Built with nvcc and run on the host by tests/test_split_geometry.py;
-// it launches no kernel.
+// lengths, P x = b and Pbar x = b solved with the stored factors agree with a dense Gaussian
+// elimination of the same App. A matrices, assembled from their row functions -- both as one
+// elimination over the whole line and as the chunked, halo-truncated elimination the prologue
+// kernel runs (prologue_win_solve, called here on the host for every chunk), which must cover
+// every row once and agree to 1e-13.  Built with nvcc and run on the host by
+// tests/test_split_geometry.py; it launches no kernel.
 #include "../paper_2006_07583_gb300/csrc/adi_kernels.cu"
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -35,7 +38,7 @@ static std::vector<double> dense_solve(std::vector<double> A, std::vector<double
 
 int main() {
     int bad = 0;
-    for (int N : {16, 17, 31, 64, 100, 257}) {
+    for (int N : {16, 17, 31, 64, 65, 95, 96, 97, 100, 127, 128, 129, 257, 1001}) {
         std::vector<double> f;
         prologue_factors(N, f);
         for (int bar = 0; bar < 2; ++bar) {
@@ -59,6 +62,21 @@ int main() {
             double err = 0.0, nrm = 0.0;
             for (int r = 0; r < n; ++r) { err = std::fmax(err, std::fabs(x[r] - xd[r])); nrm = std::fmax(nrm, std::fabs(xd[r])); }
             if (!(err <= 1e-13 * nrm)) { printf("FAIL N %d bar %d err %g\n", N, bar, err); ++bad; }
+            // the chunked elimination of the kernel
+            const double *su_id = f.data() + 3 * (N + 1) + 3 * (N - 1);
+            std::vector<double> tmp(n, 0.0), xc(n, 0.0);
+            std::vector<int> hits(n, 0);
+            for (int r0 = 0; r0 < n; r0 += kProR) {
+                const int r1 = std::min(n, r0 + kProR);
+                prologue_win_solve<double>(n, r0, r1, b.data(), 1, lo, cu, id, su_id, tmp.data(), 1,
+                                           [&](int r, double v) { xc[r] = v; ++hits[r]; });
+            }
+            double errc = 0.0;
+            for (int r = 0; r < n; ++r) {
+                errc = std::fmax(errc, std::fabs(xc[r] - xd[r]));
+                if (hits[r] != 1) { printf("FAIL N %d bar %d row %d written %d times\n", N, bar, r, hits[r]); ++bad; }
+            }
+            if (!(errc <= 1e-13 * nrm)) { printf("FAIL chunked N %d bar %d err %g\n", N, bar, errc); ++bad; }
         }
     }
     printf("bad %d\n", bad);

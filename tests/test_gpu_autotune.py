@@ -64,3 +64,43 @@ def test_autotune_rejects_bad_arguments(adi):
     with pytest.raises(adi.AdiError):
         s.autotune(trials=0)
     s.close()
+
+
+@pytest.mark.parametrize("method,nx,ny,prec", [(wl.CFD, 300, 220, 0), (wl.MFD, 260, 197, 0),
+                                               (wl.CFD, 130, 700, 1), (wl.MFD, 1024, 128, 0)])
+def test_launch_parameters_leave_results_unchanged(adi, method, nx, ny, prec):
+    """Every lines-per-CTA cap and ring depth of the factored solver gives the same numbers as
+    the automatic launch: each line is solved by the same arithmetic whatever its group."""
+    sp = wl.seismic_spec(method, nx, ny, 6, h=5.0, seed=31 + nx)
+    ref = _sim(adi, sp, prec)
+    assert ref.solver == adi.ADI_SOLVER_FACTORED
+    ref.step(6)
+    want = ref.read()
+    ref.close()
+    for cap in (1, 2, 3, 7):
+        for ring in (1, 2):
+            s = _sim(adi, sp, prec)
+            s.set_launch(cap, ring)
+            assert s.launch() == (cap, 1 if ring == 1 else 0)
+            s.step(6)
+            for g, w in zip(s.read(), want):
+                assert np.array_equal(g, w)
+            s.close()
+
+
+def test_autotune_chooses_launch_parameters(adi):
+    """On short lines (many per CTA) the tuner times the factored solver's launch parameters too;
+    the chosen ones are reported and the fields stay exactly as they were."""
+    sp = wl.seismic_spec(wl.MFD, 256, 256, 10, h=5.0, seed=77)
+    s = _sim(adi, sp, 0)
+    s.step(3)
+    before = s.read()
+    chosen, ms = s.autotune(trials=4, force=True)
+    for a, b in zip(before, s.read()):
+        assert np.array_equal(a, b)
+    cap, ring = s.launch()
+    if chosen == adi.ADI_SOLVER_FACTORED:
+        assert cap >= 0 and ring in (0, 1)
+    else:
+        assert (cap, ring) == (0, 0)
+    s.close()
