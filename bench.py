@@ -384,7 +384,9 @@ def main():
            "gpu_launches": 2 * K * (len({sp.method for sp in specs}) + 1)}
 
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3))
+        out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3), f32=esz == 4)
+        if esz == 4:
+            out["e2e_fp64_host"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3), f32=False)
     if rank == 0 and not args.no_fp64:
         out["fp64_plain"] = fp64_plain(adi, args.side)
     batch.close()
@@ -472,38 +474,43 @@ def paper_leg(adi, side, steps=2, kmax=6):
             "value": pts / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps}
 
 
-def e2e_leg(adi, torch, sims, batch, specs, n):
+def e2e_leg(adi, torch, sims, batch, specs, n, f32=True):
     """Same metric through the public API with host buffers: every step uploads each
-    member's fields from pinned host memory (adi_set_fields), advances the batch one step
-    and reads the fields back (adi_read_fields); wall-clock timed."""
+    member's fields from pinned host memory (adi_set_fields_f32, or adi_set_fields with FP64
+    arrays), advances the batch one step and reads the fields back (adi_read_fields_f32 /
+    adi_read_fields); wall-clock timed."""
+    from paper_2006_07583_gb300 import workloads as wl
+
+    dt = torch.float32 if f32 else torch.float64
     bufs = []
     for sp in specs:
-        from paper_2006_07583_gb300 import workloads as wl
-
         shp = wl.shapes(sp.method, sp.nx, sp.ny)
-        bufs.append([torch.zeros(s, dtype=torch.float64, pin_memory=True).numpy() for s in shp])
+        bufs.append([torch.zeros(s, dtype=dt, pin_memory=True).numpy() for s in shp])
     h2d = sum(sum(b.nbytes for b in bb) for bb in bufs)
+    read = (lambda s, bb: s.read_into_f32(*bb)) if f32 else (lambda s, bb: s.read_into(*bb))
+    write = (lambda s, bb: s.set_fields_f32(*bb)) if f32 else (lambda s, bb: s.set_fields(*bb))
     batch.sync()
     for s, bb in zip(sims, bufs):
-        s.read_into(*bb)
+        read(s, bb)
     for s, bb in zip(sims, bufs):  # one untimed round trip: first-use buffers are set up here
-        s.set_fields(*bb)
+        write(s, bb)
     batch.step(1)
     batch.sync()
     for s, bb in zip(sims, bufs):
-        s.read_into(*bb)
+        read(s, bb)
     t0 = time.perf_counter()
     for _ in range(n):
         for s, bb in zip(sims, bufs):
-            s.set_fields(*bb)
+            write(s, bb)
         batch.step(1)
         batch.sync()
         for s, bb in zip(sims, bufs):
-            s.read_into(*bb)
+            read(s, bb)
     el = time.perf_counter() - t0
     pts = sum(sp.nx * sp.ny for sp in specs)
     return {"value": pts * n / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": h2d, "steps": n}
+            "d2h_bytes_per_step": h2d, "steps": n,
+            "api": "adi_set_fields_f32 / adi_read_fields_f32" if f32 else "adi_set_fields / adi_read_fields (FP64)"}
 
 
 def _run_server(adi, reqs, arrivals, budget=150 << 30):

@@ -224,6 +224,16 @@ int adi_read_fields(adi_handle sim, double *u, double *v, double *w);
  */
 int adi_set_fields(adi_handle sim, const double *u, const double *v, const double *w);
 
+/*
+ * adi_set_fields_f32 / adi_read_fields_f32 -- adi_set_fields and adi_read_fields with FP32
+ * host arrays (same shapes), for callers whose fields live in single precision: an FP32
+ * simulation's fields then cross the host link at half the bytes, without conversion on the
+ * host.  An FP64 simulation converts them on the device (reading rounds to FP32).  The same
+ * finite check, errors and batch behaviour as the FP64 calls.
+ */
+int adi_set_fields_f32(adi_handle sim, const float *u, const float *v, const float *w);
+int adi_read_fields_f32(adi_handle sim, float *u, float *v, float *w);
+
 /* adi_check_finite -- scans U, V, W on the device; ADI_ENONFINITE if any is NaN/Inf. */
 int adi_check_finite(adi_handle sim);
 

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libadi.so")
 _lib = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _vp = ctypes.c_void_p
 
 
@@ -66,6 +67,8 @@ _SIGS = {
     "adi_set_sponge": ([_vp, ctypes.c_double, ctypes.c_double], ctypes.c_int),
     "adi_set_launch": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "adi_get_launch": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "adi_set_fields_f32": ([_vp, _fp, _fp, _fp], ctypes.c_int),
+    "adi_read_fields_f32": ([_vp, _fp, _fp, _fp], ctypes.c_int),
     "adi_step": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_sync": ([_vp], ctypes.c_int),
     "adi_read_fields": ([_vp, _dp, _dp, _dp], ctypes.c_int),
@@ -296,6 +299,25 @@ class Sim:
         """adi_read_fields into caller-provided float64 C-contiguous arrays."""
         _check(lib().adi_read_fields(self._h, U.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
                                      W.ctypes.data_as(_dp)), "adi_read_fields")
+
+    def read_into_f32(self, U, V, W):
+        """adi_read_fields_f32 into caller-provided float32 C-contiguous arrays."""
+        for a, shp in zip((U, V, W), self.shapes):
+            if a is not None:
+                assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"] and a.shape == tuple(shp)
+        p = [a.ctypes.data_as(_fp) if a is not None else None for a in (U, V, W)]
+        _check(lib().adi_read_fields_f32(self._h, *p), "adi_read_fields_f32")
+
+    def set_fields_f32(self, U=None, V=None, W=None):
+        """adi_set_fields_f32 from float32 C-contiguous arrays (None keeps a field)."""
+        p = []
+        for a, shp in zip((U, V, W), self.shapes):
+            if a is None:
+                p.append(None)
+                continue
+            assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"] and a.shape == tuple(shp)
+            p.append(a.ctypes.data_as(_fp))
+        _check(lib().adi_set_fields_f32(self._h, *p), "adi_set_fields_f32")
 
     def check_finite(self):
         return lib().adi_check_finite(self._h)

@@ -338,6 +338,24 @@ __global__ void convert_to_double(const T *src, double *dst, size_t rows, size_t
         dst[i] = (double)src[r * ld + c];
     }
 }
+// Compact row-major S (rows x cols) -> rows with leading dimension ld in T.
+template <typename S, typename T>
+__global__ void convert_in(const S *src, T *dst, size_t rows, size_t cols, size_t ld) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < rows * cols) {
+        size_t r = i / cols, c = i - r * cols;
+        dst[r * ld + c] = (T)src[i];
+    }
+}
+// Rows with leading dimension ld in T -> compact row-major D.
+template <typename T, typename D>
+__global__ void convert_out(const T *src, D *dst, size_t rows, size_t cols, size_t ld) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < rows * cols) {
+        size_t r = i / cols, c = i - r * cols;
+        dst[i] = (D)src[r * ld + c];
+    }
+}
 
 // dst[j * ld_dst + i] = src[i * ld_src + j] for a rows x cols array (32 x 32 tiles).
 template <typename T>
@@ -963,27 +981,43 @@ int setup_solver(adi_sim *s) {
 }
 
 // The FP64 staging buffer of host <-> device field copies (one field), kept once allocated.
+// Byte offsets of the three fields' slots in the staging buffer (U, V, W; FP64-sized).
+void xfer_slots(const Geometry &g, size_t off[4]) {
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    off[0] = 0;
+    off[1] = up(g.nU() * sizeof(double));
+    off[2] = off[1] + up(g.nV() * sizeof(double));
+    off[3] = off[2] + up(g.nW() * sizeof(double));
+}
 int xfer_buffer(adi_sim *s) {
-    const Geometry &g = s->g;
-    const size_t bytes = std::max(g.nU(), std::max(g.nV(), g.nW())) * sizeof(double);
-    if (s->xfer.bytes >= bytes) return ADI_OK;
+    size_t off[4];
+    xfer_slots(s->g, off);
+    if (s->xfer.bytes >= off[3]) return ADI_OK;
     dev_free(s->xfer);
-    return dev_alloc(s->xfer, bytes);
+    return dev_alloc(s->xfer, off[3]);
 }
 
-// Finite check of host fields on the device, before any of the simulation's state changes:
-// each field is copied into the staging buffer and scanned there (ADI_EINVAL on NaN/Inf).
-int check_finite_on_device(adi_sim *s, const double *u, const double *v, const double *w) {
+// Copies host fields (FP64, or FP32 with f32) into their slots of the staging buffer and checks
+// them there, before any of the simulation's state changes (ADI_EINVAL on NaN/Inf).  staged[k]
+// receives the slot of field k, or nullptr for a field not given.
+int stage_fields(adi_sim *s, const void *const f[3], bool f32, const void *staged[3]) {
     int rc = xfer_buffer(s);
     if (rc) return rc;
     const Geometry &g = s->g;
-    const double *f[3] = {u, v, w};
+    size_t off[4];
+    xfer_slots(g, off);
     const size_t n[3] = {g.nU(), g.nV(), g.nW()};
+    const size_t hsz = f32 ? sizeof(float) : sizeof(double);
     cudaError_t e = cudaMemsetAsync(s->status.p, 0, sizeof(int), s->stream);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        staged[k] = nullptr;
         if (!f[k]) continue;
-        e = cudaMemcpyAsync(s->xfer.p, f[k], n[k] * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = launch_finite_check<double>((const double *)s->xfer.p, n[k], (int *)s->status.p, s->stream);
+        void *slot = (unsigned char *)s->xfer.p + off[k];
+        e = cudaMemcpyAsync(slot, f[k], n[k] * hsz, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = f32 ? launch_finite_check<float>((const float *)slot, n[k], (int *)s->status.p, s->stream)
+                    : launch_finite_check<double>((const double *)slot, n[k], (int *)s->status.p, s->stream);
+        staged[k] = slot;
     }
     int flag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, s->status.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
@@ -992,20 +1026,34 @@ int check_finite_on_device(adi_sim *s, const double *u, const double *v, const d
     return flag ? ADI_EINVAL : ADI_OK;
 }
 
-// Loads natural fields (host; NULL keeps the current natural value) into both ping-pong
-// copies and rebuilds the carried state at the current parity with the prologue (so a
-// member of a batch stays consistent with the batch's plan).
-int load_state(adi_sim *s, const double *u, const double *v, const double *w, bool keep_missing) {
+// One staged field (compact rows x cols of FP64, or FP32 with f32) into a device array of the
+// simulation's precision with leading dimension ld; nullptr: zeros.
+int load_field(adi_sim *s, const void *staged, bool f32, void *dst, size_t rows, size_t cols, size_t ld) {
+    if (!staged) return cuda_status(cudaMemsetAsync(dst, 0, rows * ld * s->esz, s->stream));
+    const unsigned blocks = (unsigned)((rows * cols + 255) / 256);
+    if (s->precision == ADI_FP64) {
+        if (f32) convert_in<float, double><<<blocks, 256, 0, s->stream>>>((const float *)staged, (double *)dst, rows, cols, ld);
+        else convert_in<double, double><<<blocks, 256, 0, s->stream>>>((const double *)staged, (double *)dst, rows, cols, ld);
+    } else {
+        if (f32) convert_in<float, float><<<blocks, 256, 0, s->stream>>>((const float *)staged, (float *)dst, rows, cols, ld);
+        else convert_in<double, float><<<blocks, 256, 0, s->stream>>>((const double *)staged, (float *)dst, rows, cols, ld);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+// Loads natural fields (staged device copies from stage_fields; nullptr keeps the current
+// natural value, or zeros without keep_missing) into both ping-pong copies and rebuilds the
+// carried state at the current parity with the prologue (so a member of a batch stays
+// consistent with the batch's plan).
+int load_state(adi_sim *s, const void *const staged[3], bool f32, bool keep_missing) {
     const Geometry &g = s->g;
     const size_t esz = s->esz;
-    int rc = xfer_buffer(s);
-    if (rc) return rc;
-    DevBuf &staging = s->xfer;
     const int cur = s->parity;
-    if (v || !keep_missing) rc = upload(s, v, s->V[cur].p, g.rows_v, g.ldv, g.ldvp, (double *)staging.p, 1.0, 0);
+    int rc = ADI_OK;
+    if (staged[1] || !keep_missing) rc = load_field(s, staged[1], f32, s->V[cur].p, g.rows_v, g.ldv, g.ldvp);
     if (!rc) rc = cuda_status(cudaMemcpyAsync(s->V[1 - cur].p, s->V[cur].p, g.nVp() * esz, cudaMemcpyDeviceToDevice, s->stream));
-    if (!rc && (u || !keep_missing)) rc = upload(s, u, s->Uo.p, g.rows_u, g.ldu, g.ldu, (double *)staging.p, 1.0, 0);
-    if (!rc && (w || !keep_missing)) rc = upload(s, w, s->Wo.p, g.rows_w, g.ldw, g.ldw, (double *)staging.p, 1.0, 0);
+    if (!rc && (staged[0] || !keep_missing)) rc = load_field(s, staged[0], f32, s->Uo.p, g.rows_u, g.ldu, g.ldu);
+    if (!rc && (staged[2] || !keep_missing)) rc = load_field(s, staged[2], f32, s->Wo.p, g.rows_w, g.ldw, g.ldw);
     // with time-harmonic walls, u's walls are the harmonic data at the current time
     if (!rc) rc = harm_self(s, 2);
     // all four carried-pressure arrays start from u (their outer rows/columns stay the
@@ -1148,7 +1196,11 @@ int adi_create(adi_handle *out, int method, int nx, int ny, double h, double dt,
         dev_free(staging);
     }
     if (!rc) rc = setup_solver(s);
-    if (!rc) rc = load_state(s, u0, v0, w0, false);
+    if (!rc) {
+        const void *f[3] = {u0, v0, w0}, *staged[3];
+        rc = stage_fields(s, f, false, staged);
+        if (!rc) rc = load_state(s, staged, false, false);
+    }
     if (rc) { adi_destroy(s); return rc; }
     dev_free(s->xfer);  // set-up staging is not kept
     dev_free(s->pro);
@@ -1406,7 +1458,10 @@ int adi_set_harmonic(adi_handle s, const double *B, const double *F, double omeg
     if (!rc) rc = upload_sim_descs(s);
     if (!rc) rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
     s->plan_base = s->parity;
-    if (!rc) rc = load_state(s, nullptr, nullptr, nullptr, true);
+    if (!rc) {
+        const void *none[3] = {nullptr, nullptr, nullptr};
+        rc = load_state(s, none, false, true);
+    }
     dev_free(s->xfer);
     dev_free(s->pro);
     if (rc) s->sticky = rc;
@@ -1550,7 +1605,9 @@ int adi_read_fields(adi_handle s, double *u, double *v, double *w) {
     return ADI_OK;
 }
 
-int adi_set_fields(adi_handle s, const double *u, const double *v, const double *w) {
+namespace {
+// adi_set_fields / adi_set_fields_f32: stage and check every given field, then load them.
+int set_fields_any(adi_handle s, const void *u, const void *v, const void *w, bool f32) {
     if (!s) return ADI_EINVAL;
     if (s->in_batch && s->batch_stream) {
         cudaError_t be = cudaStreamSynchronize(s->batch_stream);
@@ -1558,12 +1615,60 @@ int adi_set_fields(adi_handle s, const double *u, const double *v, const double 
     }
     int rc = adi_sync(s);
     if (rc) return rc;
-    rc = check_finite_on_device(s, u, v, w);
+    const void *f[3] = {u, v, w}, *staged[3];
+    rc = stage_fields(s, f, f32, staged);
     if (rc == ADI_EINVAL) return rc;
     if (rc) return s->sticky = rc;
-    rc = load_state(s, u, v, w, true);
+    rc = load_state(s, staged, f32, true);
     if (rc) s->sticky = rc;
     return rc;
+}
+}  // namespace
+
+int adi_set_fields(adi_handle s, const double *u, const double *v, const double *w) {
+    return set_fields_any(s, u, v, w, false);
+}
+
+int adi_set_fields_f32(adi_handle s, const float *u, const float *v, const float *w) {
+    return set_fields_any(s, u, v, w, true);
+}
+
+int adi_read_fields_f32(adi_handle s, float *u, float *v, float *w) {
+    if (!s) return ADI_EINVAL;
+    if (s->in_batch && s->batch_stream) {
+        cudaError_t be = cudaStreamSynchronize(s->batch_stream);
+        if (be != cudaSuccess) return s->sticky = cuda_status(be);
+    }
+    int rc = adi_sync(s);
+    if (rc) return rc;
+    const Geometry &g = s->g;
+    struct { const void *src; float *dst; size_t rows, cols, ld; } parts[3] = {
+        {s->Uo.p, u, (size_t)g.rows_u, (size_t)g.ldu, (size_t)g.ldu},
+        {s->V[s->parity].p, v, (size_t)g.rows_v, (size_t)g.ldv, (size_t)g.ldvp},
+        {s->Wo.p, w, (size_t)g.rows_w, (size_t)g.ldw, (size_t)g.ldw}};
+    if (s->precision == ADI_FP64) {
+        rc = xfer_buffer(s);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto &pt : parts) {
+        if (!pt.dst || e != cudaSuccess) continue;
+        if (s->precision == ADI_FP32) {  // straight from the device arrays (rows of ld elements)
+            e = cudaMemcpy2DAsync(pt.dst, pt.cols * sizeof(float), pt.src, pt.ld * sizeof(float), pt.cols * sizeof(float),
+                                  pt.rows, cudaMemcpyDeviceToHost, s->stream);
+        } else {
+            const size_t n = pt.rows * pt.cols;
+            convert_out<double, float><<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>((const double *)pt.src,
+                                                                                          (float *)s->xfer.p, pt.rows,
+                                                                                          pt.cols, pt.ld);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(pt.dst, s->xfer.p, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the staging is reused
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->sticky = cuda_status(e);
+    return ADI_OK;
 }
 
 int adi_check_finite(adi_handle s) {

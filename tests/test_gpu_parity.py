@@ -312,3 +312,35 @@ def test_set_fields_rejects_nonfinite_and_keeps_state(adi):
             assert np.array_equal(a, b)
     s.set_fields(*before)  # finite inputs are accepted
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fp32_host_field_calls(adi, precision):
+    """adi_set_fields_f32 / adi_read_fields_f32: the same state as the FP64 calls on values that
+    FP32 holds exactly, reads equal to the FP64 read rounded to FP32, and a NaN input rejected
+    with the fields untouched."""
+    method, nx, ny = MFD, 45, 38
+    h, dt, c, U, V, W = _random_case(method, nx, ny, seed=515)
+    U32, V32, W32 = (x.astype(np.float32) for x in (U, V, W))
+    a = adi.Sim(method, nx, ny, h, dt, c, precision=precision)
+    b = adi.Sim(method, nx, ny, h, dt, c, precision=precision)
+    a.set_fields(*(x.astype(np.float64) for x in (U32, V32, W32)))
+    b.set_fields_f32(U32, V32, W32)
+    a.step(3)
+    b.step(3)
+    ra = a.read()
+    for x, y in zip(ra, b.read()):
+        assert np.array_equal(x, y)
+    out = [np.empty(s, dtype=np.float32) for s in b.shapes]
+    b.read_into_f32(*out)
+    for x, y in zip(out, ra):
+        assert np.array_equal(x, y.astype(np.float32))
+    bad = [o.copy() for o in out]
+    bad[1][2, 3] = np.nan
+    with pytest.raises(adi.AdiError) as e:
+        b.set_fields_f32(*bad)
+    assert e.value.code == 1
+    for x, y in zip(b.read(), ra):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
