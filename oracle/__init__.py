@@ -70,6 +70,7 @@ def _load():
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
             dp, dp, dp, ctypes.c_int, ctypes.c_double, dp, dp, dp, ctypes.c_double,
             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+            ctypes.c_double, ctypes.c_double,
         ]
         lib.oracle_run_harmonic.restype = ctypes.c_int
         lib.oracle_run_sponge.argtypes = [
@@ -155,10 +156,12 @@ def run(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0=0.0, source=None, kmax
 
 
 def run_harmonic(method, nx, ny, h, dt, kappa, U, V, W, nsteps, B, F=None, omega=1.0,
-                 phase_b=0.0, phase_f=0.0, t0=0.0, source=None, kmax=0, eps=0.0, threads=1):
+                 phase_b=0.0, phase_f=0.0, t0=0.0, source=None, kmax=0, eps=0.0, threads=1,
+                 sponge=None):
     """run() with time-harmonic Dirichlet data u = B cos(omega t + phase_b) on U's walls and
     forcing f = F cos(omega t + phase_f) at the interior pressure points (Eq. 11's problem).
-    U must hold the walls at t0."""
+    U must hold the walls at t0.  sponge: None or (width, a), the absorbing layers of
+    run_sponge after every step."""
     su, sv, sw = field_shapes(method, nx, ny)
     kappa = np.ascontiguousarray(kappa, dtype=np.float64)
     U = np.array(U, dtype=np.float64, order="C", copy=True)
@@ -177,7 +180,9 @@ def run_harmonic(method, nx, ny, h, dt, kappa, U, V, W, nsteps, B, F=None, omega
                                      _ptr(W), int(nsteps), float(t0),
                                      _ptr(src) if src is not None else None, _ptr(B), Fp,
                                      float(omega), float(phase_b), float(phase_f), int(kmax),
-                                     float(eps), int(threads))
+                                     float(eps), int(threads),
+                                     float(sponge[0]) if sponge else 0.0,
+                                     float(sponge[1]) if sponge else 0.0)
     if rc:
         raise RuntimeError("oracle_run_harmonic failed: %d" % rc)
     return U, V, W

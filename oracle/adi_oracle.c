@@ -865,15 +865,18 @@ int oracle_run_sponge(int method, int nx, int ny, double h, double dt, const dou
  *   F      U-shaped or NULL; f = F cos(omega t + phf) at the interior pressure points, added
  *          as Eqs. 6-7 add the source (dt/2 f(t_m) in stage 1, dt/2 f(t_{m+1}) in stage 2).
  * The intermediate u* at the x-line ends (west and east walls) is u0(t_m + dt/2); the
- * y-line ends (south and north walls) take u0(t_{m+1}). */
+ * y-line ends (south and north walls) take u0(t_{m+1}).  sponge_width, sponge_a > 0 add the
+ * absorbing layers of oracle_run_sponge after every step. */
 int oracle_run_harmonic(int method, int nx, int ny, double h, double dt, const double *kappa,
                         double *U, double *V, double *W, int nsteps, double t0,
                         const double *src, const double *B, const double *F, double omega,
-                        double phb, double phf, int kmax, double eps, int nthreads) {
-    if (!B) return -1;
+                        double phb, double phf, int kmax, double eps, int nthreads,
+                        double sponge_width, double sponge_a) {
+    if (!B || !(sponge_width >= 0.0) || !(sponge_a >= 0.0)) return -1;
     harm_t hb = {B, F, omega, phb, phf};
+    sponge_t sp = {sponge_width, sponge_a};
     return run_all(method, nx, ny, h, dt, kappa, U, V, W, nsteps, t0, src, &hb, kmax, eps,
-                   nthreads, NULL, NULL);
+                   nthreads, NULL, sponge_width > 0.0 && sponge_a > 0.0 ? &sp : NULL);
 }
 
 int oracle_num_threads(void) {
