@@ -86,3 +86,36 @@ def test_submit_rejects_busy_and_bad_arguments(adi):
         adi.batch_poll(123456)
     for s in sims:
         s.close()
+
+
+def test_submit_with_harmonic_and_layer_members(adi):
+    """Members with time-harmonic walls and forcing, with absorbing layers, and plain ones, each
+    with its own step count in one asynchronous batch: every member ends exactly where it ends
+    stepped alone (the phases rebuild the plan as members leave)."""
+    specs = _specs(9)
+    steps = [sp.steps for sp in specs]
+
+    def make(k):
+        sp = specs[k]
+        s = _make(adi, sp)
+        su = wl.shapes(sp.method, sp.nx, sp.ny)[0]
+        rng = np.random.default_rng(100 + k)
+        if k % 3 == 1:
+            s.set_harmonic(rng.standard_normal(su), rng.standard_normal(su), 40.0, 0.3, 1.1)
+        elif k % 3 == 2:
+            s.set_sponge(12.0, 0.05)
+        return s
+
+    sims = [make(k) for k in range(len(specs))]
+    t = adi.batch_submit(sims, steps)
+    deadline = time.time() + 60
+    while not adi.batch_poll(t):
+        assert time.time() < deadline
+        time.sleep(0.001)
+    for k, s in enumerate(sims):
+        r = make(k)
+        r.step(steps[k])
+        for x, y in zip(s.read(), r.read()):
+            assert np.array_equal(x, y), k
+        r.close()
+        s.close()
