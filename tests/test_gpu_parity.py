@@ -344,3 +344,22 @@ def test_fp32_host_field_calls(adi, precision):
         assert np.array_equal(x, y)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("method", [CFD, MFD])
+def test_source_set_after_steps_follows_the_clock(adi, method):
+    """A Ricker source switched on after some source-free steps is evaluated at the simulation's
+    own time (the device step clock follows the step count), as the oracle started at t0."""
+    nx, ny = 40, 36
+    h, dt, c, U, V, W = _random_case(method, nx, ny, seed=77)
+    src = (ny // 2, nx // 2, 2.0, 9.0, 0.03)
+    s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=adi.ADI_FP64)
+    s.step(5)
+    s.set_source(*src)
+    s.step(4)
+    G = s.read()
+    s.close()
+    O = oracle.run(method, nx, ny, h, dt, c ** 2, U, V, W, 5)
+    O = oracle.run(method, nx, ny, h, dt, c ** 2, *O, 4, t0=5 * dt, source=src)
+    for g, o in zip(G, O):
+        assert _max_rel(g, o) <= 1e-12
