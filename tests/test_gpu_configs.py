@@ -246,3 +246,32 @@ def test_8192_fp32_heterogeneous_one_step_against_fp64_line_solver(adi, method):
         s.close()
     for a, b in zip(out[0], out[1]):
         assert _l2_rel(a, b) <= 1e-4
+
+
+@pytest.mark.parametrize("method", [CFD, MFD])
+def test_maximum_line_length(adi, method):
+    """Lines of the maximum length (ADI_MAX_CELLS = 16384 cells, split into four sub-lines by the
+    factored solver) on a 16384 x 16 grid with random fields, media and walls: the default solver
+    in FP64 against the FP64 thread-per-line solver (an independent kernel pinned to the oracle)
+    to 1e-12, and in FP32 to 1e-4 relative L2, over 3 steps."""
+    nx, ny = 16384, 16
+    rng = np.random.default_rng(60 + method)
+    su, sv, sw = wl.shapes(method, nx, ny)
+    h = 1.0 / nx
+    c = rng.uniform(0.6, 1.4, su)
+    U, V, W = rng.standard_normal(su), rng.standard_normal(sv), rng.standard_normal(sw)
+    dt = 0.8 * h / c.max()
+    out = {}
+    for key, prec, solver in (("ref", adi.ADI_FP64, adi.ADI_SOLVER_LINE), ("fp64", adi.ADI_FP64, None),
+                              ("fp32", adi.ADI_FP32, None)):
+        kw = {} if solver is None else {"solver": solver}
+        s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=prec, **kw)
+        if solver is None:
+            assert s.solver == adi.ADI_SOLVER_FACTORED
+        s.step(3)
+        out[key] = s.read()
+        s.close()
+    for a, r in zip(out["fp64"], out["ref"]):
+        assert np.max(np.abs(a - r)) <= 1e-12 * np.max(np.abs(r))
+    for a, r in zip(out["fp32"], out["ref"]):
+        assert _l2_rel(a, r) <= 1e-4
