@@ -173,3 +173,20 @@ def test_eq11_gamma9_rate_about_two_on_gpu(adi, method, Ns):
     r = oracle.rates(errs, Ns)
     assert 1.5 < oracle.trimmed_mean(r) < 2.8, (errs, r)
     assert 1.3 < r[-1] < 2.8, (errs, r)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_harmonic_split_lines_vs_oracle(adi, precision):
+    """4700-cell x-lines (split into sub-lines by the factored solver) with time-harmonic walls
+    and forcing."""
+    method, nx, ny = wl.MFD, 4700, 24
+    h, dt, c, U, V, W, B, F, om, pb, pf = _case(method, nx, ny, seed=4724)
+    s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=precision)
+    assert s.solver == adi.ADI_SOLVER_FACTORED
+    s.set_harmonic(B, F, om, pb, pf)
+    s.step(3)
+    G = s.read()
+    s.close()
+    O = oracle.run_harmonic(method, nx, ny, h, dt, c ** 2, U, V, W, 3, B, F, om, pb, pf,
+                            threads=max(1, oracle.num_threads()))
+    _check(G, O, precision)

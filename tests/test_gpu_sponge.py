@@ -172,3 +172,19 @@ def test_pulse_energy_absorbed_at_1024(adi, method):
     if method == MFD:
         assert 0.9 < out[False] < 1.1, out
     assert out[True] < 0.01, out
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_sponge_split_lines_vs_oracle(adi, precision):
+    """4700-cell x-lines (split into sub-lines by the factored solver) with absorbing layers."""
+    method, nx, ny = CFD, 4700, 24
+    h, dt, c, U, V, W = _case(method, nx, ny, seed=4747)
+    s = adi.Sim(method, nx, ny, h, dt, c, U, V, W, precision=precision)
+    assert s.solver == adi.ADI_SOLVER_FACTORED
+    s.set_sponge(30.0, 0.04)
+    s.step(2)
+    G = s.read()
+    s.close()
+    O = oracle.run_sponge(method, nx, ny, h, dt, c ** 2, U, V, W, 2, 30.0, 0.04,
+                          threads=max(1, oracle.num_threads()))
+    _check(G, O, precision)
