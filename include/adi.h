@@ -106,6 +106,15 @@ int adi_set_solver(adi_handle sim, int solver);
 int adi_get_solver(adi_handle sim);
 
 /*
+ * adi_get_scan_reach -- the factored solver's chunk-joining reach (a property of the solver,
+ * not of the paper): the largest number of consecutive chunks, over the handle's lines, whose
+ * transfer product still exceeds the neglect threshold (2^-40 for FP32 records, 2^-70 for
+ * FP64).  Lines of a handle whose reach is above 32 join their chunks with full log-depth scans
+ * instead of windowed ones.  *reach = 0 for the other solvers.  Errors: ADI_EINVAL (NULL).
+ */
+int adi_get_scan_reach(adi_handle sim, int *reach);
+
+/*
  * adi_autotune -- picks the line solver of a handle by measurement.  Every solver the
  * configuration supports (ADI_SOLVER_FACTORED, _CHUNKED, _LINE: the chunk-parallel solves and
  * the thread-per-line Thomas-style elimination) runs `trials` steps (rounded up to an even

@@ -53,6 +53,7 @@ _SIGS = {
     "adi_set_stream": ([_vp, _vp], ctypes.c_int),
     "adi_set_solver": ([_vp, ctypes.c_int], ctypes.c_int),
     "adi_get_solver": ([_vp], ctypes.c_int),
+    "adi_get_scan_reach": ([_vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "adi_autotune": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp], ctypes.c_int),
     "adi_selftest_wait_timeout": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)],
                                   ctypes.c_int),
@@ -255,6 +256,13 @@ class Sim:
     @property
     def solver(self):
         return lib().adi_get_solver(self._h)
+
+    @property
+    def scan_reach(self):
+        """adi_get_scan_reach: the factored solver's largest chunk-joining reach (0 otherwise)."""
+        r = ctypes.c_int()
+        _check(lib().adi_get_scan_reach(self._h, ctypes.byref(r)), "adi_get_scan_reach")
+        return r.value
 
     def autotune(self, trials=2, force=False):
         """adi_autotune: times every usable solver on this simulation's own state (restored

@@ -187,7 +187,6 @@ struct Plan {
     size_t fstage[2][kFacVariants] = {};  // shared memory of one pipeline stage
     int fstages[2][kFacVariants] = {};    // pipeline depth (2 = prefetch)
     int fgrid[2][kFacVariants] = {};      // persistent CTAs
-    int freach[2][kFacVariants] = {};     // largest scan reach of the launch's lines
     int fring[2][kFacVariants] = {};      // ring-depth cap of the launch (0: none)
     // carried-pressure transposes after each stage, one array per member: [dir]
     DevBuf tdesc[2];
@@ -229,7 +228,6 @@ void plan_free(Plan &p) {
             p.fstage[d][v] = 0;
             p.fstages[d][v] = 0;
             p.fgrid[d][v] = 0;
-            p.freach[d][v] = 0;
             p.fring[d][v] = 0;
         }
         p.v1n[d] = 0;
@@ -601,11 +599,13 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
                     if (s->fac_nl_cap > 0) nl = std::min(nl, s->fac_nl_cap);
                     for (int st = 0; st < n; st += nl) {
                         int cnt = std::min(nl, n - st);
-                        fgr[dir][v].push_back(fac_group_of(s->g.method, N, first + st, cnt, 1.0 / s->h, 0.5 * s->dt));
+                        FacGroup fg = fac_group_of(s->g.method, N, first + st, cnt, 1.0 / s->h, 0.5 * s->dt);
+                        // the scans this simulation's lines need, whatever else shares the launch
+                        if (s->fac_reach > kFacMaxReach) fg.own |= kFacOwnFull;
+                        fgr[dir][v].push_back(fg);
                         p.fstage[dir][v] = std::max(p.fstage[dir][v], fac_stage_bytes(s->g.method, N, cnt, esz));
                     }
                 }
-                p.freach[dir][v] = std::max(p.freach[dir][v], s->fac_reach);
                 if (s->fac_ring_cap > 0)
                     p.fring[dir][v] = p.fring[dir][v] > 0 ? std::min(p.fring[dir][v], s->fac_ring_cap) : s->fac_ring_cap;
                 for (int q = 0; q < 2; ++q) {
@@ -767,7 +767,7 @@ cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream
             e = launch_line_solve_factored<T>((const LineDesc<T> *)p.fd[q][dir].p,
                                               (const FacGroup *)p.fgroups[dir][v].p, p.nfgroups[dir][v], v,
                                               p.fstage[dir][v], p.fstages[dir][v], p.fgrid[dir][v], nat,
-                                              p.freach[dir][v], (int *)p.fault.p, stream);
+                                              (int *)p.fault.p, stream);
     for (int m = 0; m < 2 && e == cudaSuccess; ++m)
         if (p.ngroups[dir][m])
             e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
@@ -1225,6 +1225,12 @@ int adi_set_solver(adi_handle s, int solver) {
 }
 
 int adi_get_solver(adi_handle s) { return s ? s->solver : -1; }
+
+int adi_get_scan_reach(adi_handle s, int *reach) {
+    if (!s || !reach) return ADI_EINVAL;
+    *reach = s->solver == ADI_SOLVER_FACTORED ? s->fac_reach : 0;
+    return ADI_OK;
+}
 
 }  // extern "C"
 

@@ -31,7 +31,8 @@
 // FP32 records, 2^-70 for FP64).  The scan value of chunk c is then the sequential recurrence
 // over the R chunks before (after) it, read from shared memory; what it leaves out is that
 // product times a true value of the solution, i.e. below tau relative to the solution.  Lines
-// whose reach exceeds kFacMaxReach use the full log-depth scan of affine maps instead.
+// whose reach exceeds kFacMaxReach use the full log-depth scan of affine maps instead (the
+// group's kFacOwnFull bit, set on the host from the line's own reach).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,12 +50,16 @@ constexpr int kFacMaxT = kFacWorkers;         // chunks (threads) per line at mo
 constexpr size_t kFacSmemLimit = 227 * 1024;  // shared memory per CTA
 constexpr size_t kFacStaticBase = 4096;       // reserve for the kernel's other static shared memory
 constexpr int kFacWs = 1024;                  // FP64 workspace of the precompute, per line
-constexpr int kFacMaxReach = 32;              // longest window of the windowed scans
 // Static shared memory of the kernel for element size esz: the scan buffers (chunk offsets,
 // two arrays for FP32, one for FP64) plus the rest.
 __host__ __device__ inline size_t fac_static_smem(size_t esz) {
     return kFacStaticBase + (size_t)kFacThreads * 3 * (esz == 4 ? 2 : 1) * esz;
 }
+
+// One rounding for a*b + c, written out so that the compiler's contraction choices cannot make
+// two code paths of the same output round differently.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // ---------------------------------------------------------------------------------------
 // Geometry of a line for the factored solver.
@@ -921,7 +926,7 @@ __device__ __forceinline__ void win_scan(bool forward, int c, int tact, int reac
 // threads per line; thread (l, c) = (tid / Tl, tid % Tl) owns middle blocks [c MM, c MM + MM).
 // ---------------------------------------------------------------------------------------
 template <typename T, int BS, int MM, bool SPLIT>
-__device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural, int full_scan, ScanSmem<T, BS> &ssm,
+__device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural, ScanSmem<T, BS> &ssm,
                                           T *offf, T *offb) {
     static_assert(MM >= 2, "chunks of at least two blocks");
     using E = FacEnd<BS>;
@@ -938,6 +943,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     // a sub-line of a split line (SPLIT) covers the chunks c0 .. c0 + tact - 1 of its line
     const int cg = SPLIT ? gr.c0 + c : c;  // global chunk
     const int own = gr.own, ol0 = own & 511, ol1 = (own >> 9) & 511;
+    const bool full_scan = (own & kFacOwnFull) != 0;
     const bool has_head = !SPLIT || (own & kFacOwnHead) != 0, has_tail = !SPLIT || (own & kFacOwnTail) != 0;
     const bool line_ok = l < gr.nl;
     const bool act = line_ok && c < tact;
@@ -1324,13 +1330,21 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
         if (staged_p(src_k)) sPw[src_k] += s; else gpo[src_k * spo] = gpo[src_k * spo] + s;
         if (d.advance_clock) *d.clock = m + 1;
     };
+    // the fourth-order staggered difference of four consecutive values, up to the factor 1/h
+    auto d4 = [](T a, T b, T c, T d) {
+        return fma_rn(T(-1.0 / 24.0), d, fma_rn(T(9.0 / 8.0), c, fma_rn(T(-9.0 / 8.0), b, T(1.0 / 24.0) * a)));
+    };
     auto out_p = [&](int k, T val_out, T val_nat) {
         if (staged_p(k)) sPw[k] = val_out; else gpo[k * spo] = val_out;
         if (uo) uo[k * snp] = val_nat;
     };
-    auto out_v = [&](int j, T vin, T dv) {  // dv = beta * (D_u u*)_j
-        if (staged_v(j)) sOut[j] = vin - T(2) * dv; else gvo[j * svo] = vin - T(2) * dv;
-        if (wo) wo[j * snv] = vin - dv;
+    // v' = v - 2 c g and the natural w = v - c g, with g the velocity's derivative term and c its
+    // factor (beta for CFD, beta/h for MFD).  The carried value is formed exactly as on the
+    // staged-only paths below, so that writing natural outputs never changes the trajectory.
+    auto out_v = [&](int j, T vin, T cf, T g) {
+        const T val = fma_rn(-(T(2) * cf), g, vin);
+        if (staged_v(j)) sOut[j] = val; else gvo[j * svo] = val;
+        if (wo) wo[j * snv] = fma_rn(-cf, g, vin);
     };
     if (owned) {
         if constexpr (BS == 2) {
@@ -1344,19 +1358,18 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 for (int i = 0; i < MM; ++i) {
                     const T ae = aw[i + 1] * inv_c3 * Y[i][0];
                     sPw[jb + i] = wp[i] - T(2) * ae;
-                    sOut[jb + i] = wv[i] - T(2) * beta * Y[i][1];
+                    sOut[jb + i] = fma_rn(-(T(2) * beta), Y[i][1], wv[i]);
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < MM; ++i) {
                     const T ae = aw[i + 1] * inv_c3 * Y[i][0];
                     out_p(jb + i, wp[i] - T(2) * ae, wp[i] - ae);
-                    out_v(jb + i, wv[i], beta * Y[i][1]);
+                    out_v(jb + i, wv[i], beta, Y[i][1]);
                 }
             }
             if (src_k >= jb && src_k < jb + MM) add_source();
         } else {
-            const T w0 = T(1.0 / 24.0), w1 = T(-9.0 / 8.0), w2 = T(9.0 / 8.0), w3 = T(-1.0 / 24.0);
             const T bi = beta * ih;
             if (stage_v && !uo && !wo && !edge) {
                 // staged outputs only: no per-point branches; the velocities after the last
@@ -1370,13 +1383,13 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                     const T xn0 = i + 1 < MM ? Y[i + 1 < MM ? i + 1 : i][0] : xin[0];
                     const T xn1 = i + 1 < MM ? Y[i + 1 < MM ? i + 1 : i][1] : xin[1];
                     const T xn2 = i + 1 < MM ? Y[i + 1 < MM ? i + 1 : i][2] : xin[2];
-                    const T d1 = w0 * Y[i][0] + w1 * Y[i][1] + w2 * Y[i][2] + w3 * xn0;
-                    const T d2 = w0 * Y[i][1] + w1 * Y[i][2] + w2 * xn0 + w3 * xn1;
-                    const T d3 = w0 * Y[i][2] + w1 * xn0 + w2 * xn1 + w3 * xn2;
+                    const T d1 = d4(Y[i][0], Y[i][1], Y[i][2], xn0);
+                    const T d2 = d4(Y[i][1], Y[i][2], xn0, xn1);
+                    const T d3 = d4(Y[i][2], xn0, xn1, xn2);
                     if (i + 1 < MM || !is_tail) {
-                        sOut[q0 + 1] = sV[q0 + 1] - b2 * d1;
-                        sOut[q0 + 2] = sV[q0 + 2] - b2 * d2;
-                        sOut[q0 + 3] = sV[q0 + 3] - b2 * d3;
+                        sOut[q0 + 1] = fma_rn(-b2, d1, sV[q0 + 1]);
+                        sOut[q0 + 2] = fma_rn(-b2, d2, sV[q0 + 2]);
+                        sOut[q0 + 3] = fma_rn(-b2, d3, sV[q0 + 3]);
                     }
                 }
                 if (src_k >= cb && src_k < cb + 3 * MM) add_source();
@@ -1392,9 +1405,9 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 const T xn1 = i + 1 < MM ? Y[in][1] : xin[1];
                 const T xn2 = i + 1 < MM ? Y[in][2] : xin[2];
                 if (!(i == MM - 1 && is_tail)) {
-                    out_v(q0 + 1, sV[q0 + 1], bi * (w0 * Y[i][0] + w1 * Y[i][1] + w2 * Y[i][2] + w3 * xn0));
-                    out_v(q0 + 2, sV[q0 + 2], bi * (w0 * Y[i][1] + w1 * Y[i][2] + w2 * xn0 + w3 * xn1));
-                    out_v(q0 + 3, sV[q0 + 3], bi * (w0 * Y[i][2] + w1 * xn0 + w2 * xn1 + w3 * xn2));
+                    out_v(q0 + 1, sV[q0 + 1], bi, d4(Y[i][0], Y[i][1], Y[i][2], xn0));
+                    out_v(q0 + 2, sV[q0 + 2], bi, d4(Y[i][1], Y[i][2], xn0, xn1));
+                    out_v(q0 + 3, sV[q0 + 3], bi, d4(Y[i][2], xn0, xn1, xn2));
                 }
             }
             if (src_k >= cb && src_k < cb + 3 * MM) add_source();
@@ -1436,7 +1449,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 if (stage_v) __syncwarp();
                 if (has) {
                     if (is_g) {
-                        out_v(node, vv, beta * x);
+                        out_v(node, vv, beta, x);
                     } else {
                         const T ae = al * x;
                         out_p(node, pp - T(2) * ae, pp - ae);
@@ -1458,7 +1471,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 if (stage_v) __syncwarp();
                 if (!has) continue;
                 if (is_g) {
-                    out_v(node, sV[node], beta * x);
+                    out_v(node, sV[node], beta, x);
                 } else {
                     const T ae = al * x;
                     out_p(node, sP[node] - T(2) * ae, sP[node] - ae);
@@ -1480,7 +1493,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 const T x = row_dot(et + (vel ? E::DZ : E::HZ) + qq * Z, vel ? E::HMAX + qq : qq);
                 if (has) {
                     if (vel) {
-                        out_v(jlo + qq, sV[jlo + qq], beta * ih * x);
+                        out_v(jlo + qq, sV[jlo + qq], beta * ih, x);
                     } else {
                         const int cc = cell0 + qq;
                         out_p(cc, T(2) * x - sP[cc], x);
@@ -1497,7 +1510,7 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
             }
             for (int q = ls; q < nrow; q += S) {
                 const int j = jlo + q;
-                out_v(j, sV[j], beta * ih * row_dot(et + E::DZ + q * Z, E::HMAX + q));
+                out_v(j, sV[j], beta * ih, row_dot(et + E::DZ + q * Z, E::HMAX + q));
             }
         }
     };
@@ -1525,7 +1538,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
 template <typename T, int BS, int MM, bool SPLIT>
 __global__ void __launch_bounds__(kFacThreads, 1)
 line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup *__restrict__ groups, int ngroups,
-                           int natural, unsigned stage_bytes, int stages, int full_scan, int *fault) {
+                           int natural, unsigned stage_bytes, int stages, int *fault) {
     extern __shared__ __align__(128) unsigned char fac_smem[];
     __shared__ ScanSmem<T, BS> ssm;
     __shared__ __align__(8) unsigned long long full[2], empty[2];
@@ -1580,7 +1593,7 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
         const int st = two ? (it & 1) : 0;
         const int use = two ? (it >> 1) : it;
         if (!mbar_wait(&full[st], (unsigned)(use & 1))) atomicExch(fault, 1);
-        fac_group<T, BS, MM, SPLIT>(fac_smem + (size_t)st * stage_bytes, natural, full_scan, ssm, offs[0], offs[kBufs - 1]);
+        fac_group<T, BS, MM, SPLIT>(fac_smem + (size_t)st * stage_bytes, natural, ssm, offs[0], offs[kBufs - 1]);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
     }
@@ -1595,29 +1608,28 @@ cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, double *ws, 
 
 template <typename T, int BS, int MM, bool SPLIT>
 cudaError_t launch_fac_inst(const LineDesc<T> *d, const FacGroup *groups, int ngroups, size_t stage_bytes, int stages,
-                            int grid, int natural, int full_scan, int *fault, cudaStream_t s) {
+                            int grid, int natural, int *fault, cudaStream_t s) {
     auto kern = line_solve_factored_kernel<T, BS, MM, SPLIT>;
     const size_t dyn = (size_t)stages * stage_bytes;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kFacThreads, dyn, s>>>(d, groups, ngroups, natural, (unsigned)stage_bytes, stages, full_scan, fault);
+    kern<<<grid, kFacThreads, dyn, s>>>(d, groups, ngroups, natural, (unsigned)stage_bytes, stages, fault);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const FacGroup *groups, int ngroups, int variant,
-                                       size_t stage_bytes, int stages, int grid, int natural, int max_reach,
-                                       int *fault, cudaStream_t s) {
+                                       size_t stage_bytes, int stages, int grid, int natural, int *fault,
+                                       cudaStream_t s) {
     if (ngroups <= 0) return cudaSuccess;
     if (grid > ngroups) grid = ngroups;
     if (stages != 1 && stages != 2) return cudaErrorInvalidValue;
-    const int full = max_reach > kFacMaxReach ? 1 : 0;
     switch (variant) {
-    case 0: return launch_fac_inst<T, 2, 9, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
-    case 1: return launch_fac_inst<T, 3, 2, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
-    case 2: return launch_fac_inst<T, 3, 3, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
-    case 3: return launch_fac_inst<T, 2, 9, true>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
-    case 4: return launch_fac_inst<T, 3, 3, true>(d, groups, ngroups, stage_bytes, stages, grid, natural, full, fault, s);
+    case 0: return launch_fac_inst<T, 2, 9, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, fault, s);
+    case 1: return launch_fac_inst<T, 3, 2, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, fault, s);
+    case 2: return launch_fac_inst<T, 3, 3, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, fault, s);
+    case 3: return launch_fac_inst<T, 2, 9, true>(d, groups, ngroups, stage_bytes, stages, grid, natural, fault, s);
+    case 4: return launch_fac_inst<T, 3, 3, true>(d, groups, ngroups, stage_bytes, stages, grid, natural, fault, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1625,9 +1637,9 @@ cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const FacGroup *gro
 template cudaError_t launch_fac_precompute<float>(const LineDesc<float> *, int, double *, int *, cudaStream_t);
 template cudaError_t launch_fac_precompute<double>(const LineDesc<double> *, int, double *, int *, cudaStream_t);
 template cudaError_t launch_line_solve_factored<float>(const LineDesc<float> *, const FacGroup *, int, int, size_t, int,
-                                                       int, int, int, int *, cudaStream_t);
+                                                       int, int, int *, cudaStream_t);
 template cudaError_t launch_line_solve_factored<double>(const LineDesc<double> *, const FacGroup *, int, int, size_t,
-                                                        int, int, int, int, int *, cudaStream_t);
+                                                        int, int, int, int *, cudaStream_t);
 
 // The bounded wait's failure path, run on purpose: one thread waits on an mbarrier that
 // nothing arrives at, with `polls` polls at most, and records whether the wait gave up (and

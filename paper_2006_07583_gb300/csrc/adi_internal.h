@@ -127,6 +127,8 @@ struct alignas(16) FacGroup {
                              // group's other owned outputs are stored by the threads that compute them
 };
 constexpr int kFacOwnHead = 1 << 18, kFacOwnTail = 1 << 19, kFacOwnSplit = 1 << 20;
+constexpr int kFacOwnFull = 1 << 21;     // the group's lines reach beyond the scan window: full scans
+constexpr int kFacMaxReach = 32;         // longest window of the windowed scans
 constexpr int kFacMaxSplit = 8;           // sub-lines of one line at most
 constexpr int kFacSplitMaxHalo = 16;      // largest scan reach a split line accepts
 FacGroup fac_group_of(int method, int N, int first, int nl, double inv_h, double beta);
@@ -148,12 +150,12 @@ size_t fac_ws_doubles();                 // FP64 workspace per line of the preco
 template <typename T>
 cudaError_t launch_fac_precompute(const LineDesc<T> *d, int nlines, double *ws, int *status,
                                   cudaStream_t s);
-// max_reach: the largest scan reach of the launch's lines (beyond the window limit the
-// kernel uses the full scan)
+// Each group takes the windowed or the full scans by its own kFacOwnFull bit, so a line's
+// arithmetic does not depend on the other lines of the launch.
 template <typename T>
 cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const FacGroup *groups, int ngroups,
                                        int variant, size_t stage_bytes, int stages, int grid,
-                                       int natural, int max_reach, int *fault, cudaStream_t s);
+                                       int natural, int *fault, cudaStream_t s);
 
 // Chunked solver (adi_chunked.cu).
 int chunk_M(int method);                 // chunk length in blocks used by the kernel
