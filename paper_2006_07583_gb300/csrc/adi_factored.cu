@@ -1085,64 +1085,91 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
     }
 
     // ---- block couplings from the alpha window ----
-    auto blockA = [&](int i, T (&A)[BS][BS]) {
-        if constexpr (BS == 2) {
-            const T tb = T(3) * ih * beta;
-            A[0][0] = T(1); A[0][1] = -tb; A[1][0] = -aw[i]; A[1][1] = T(1);
-        } else {
-            const T bh2 = beta * ih * ih;
+    // CFD: A_i = [[1, -tb], [-a_i, 1]], B = 4 I, C_i = [[1, tb], [a_{i+2}, 1]] with a = aw (3 alpha
+    // / h at the nodes) and tb = 3 beta / h; its products below are written out, so that no unit
+    // or zero entry costs an operation.  MFD: A_i (upper triangular), B_i and C_i (lower
+    // triangular) hold the 7-point operator's bands scaled per cell; its products visit the
+    // nonzero entries only (the compiler keeps a product with a literal zero).
+    const T tb = T(3) * ih * beta;
+    auto blockA = [&](int i, T (&A)[BS][BS]) {  // MFD
+        const T bh2 = beta * ih * ih;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const T sc = aw[3 * i + m] * bh2;
+        for (int m = 0; m < BS; ++m) {
+            const T sc = aw[3 * i + m] * bh2;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) A[m][q] = (q >= m) ? -sc * (T)mim_DG(q - m) : T(0);
-            }
+            for (int q = 0; q < BS; ++q) A[m][q] = (q >= m) ? -sc * (T)mim_DG(q - m) : T(0);
         }
     };
-    auto blockB = [&](int i, T (&B)[BS][BS]) {
-        if constexpr (BS == 2) {
-            B[0][0] = T(4); B[0][1] = T(0); B[1][0] = T(0); B[1][1] = T(4);
-        } else {
-            const T bh2 = beta * ih * ih;
+    auto blockB = [&](int i, T (&B)[BS][BS]) {  // MFD
+        const T bh2 = beta * ih * ih;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const T sc = aw[3 * i + m] * bh2;
+        for (int m = 0; m < BS; ++m) {
+            const T sc = aw[3 * i + m] * bh2;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) B[m][q] = (q == m ? T(1) : T(0)) - sc * (T)mim_DG(q - m + 3);
-            }
+            for (int q = 0; q < BS; ++q) B[m][q] = (q == m ? T(1) : T(0)) - sc * (T)mim_DG(q - m + 3);
         }
     };
-    auto blockC = [&](int i, T (&C)[BS][BS]) {
-        if constexpr (BS == 2) {
-            const T tb = T(3) * ih * beta;
-            C[0][0] = T(1); C[0][1] = tb; C[1][0] = aw[i + 2]; C[1][1] = T(1);
-        } else {
-            const T bh2 = beta * ih * ih;
+    auto blockC = [&](int i, T (&C)[BS][BS]) {  // MFD
+        const T bh2 = beta * ih * ih;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const T sc = aw[3 * i + m] * bh2;
+        for (int m = 0; m < BS; ++m) {
+            const T sc = aw[3 * i + m] * bh2;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) C[m][q] = (q <= m) ? -sc * (T)mim_DG(q - m + 6) : T(0);
-            }
+            for (int q = 0; q < BS; ++q) C[m][q] = (q <= m) ? -sc * (T)mim_DG(q - m + 6) : T(0);
         }
     };
-    // out = -Si (M v)
-    auto neg_si_mv = [&](const T (&Si)[BS][BS], const T (&M)[BS][BS], const T (&v)[BS], T (&out)[BS]) {
-        T t[BS];
+    // out = A_i v
+    auto mulA = [&](int i, const T (&v)[BS], T (&out)[BS]) {
+        T r[BS];
+        if constexpr (BS == 2) {
+            r[0] = v[0] - tb * v[1];
+            r[1] = v[1] - aw[i] * v[0];
+        } else {
+            T A[BS][BS];
+            blockA(i, A);
+#pragma unroll
+            for (int p = 0; p < BS; ++p) {
+                T acc = A[p][p] * v[p];
+#pragma unroll
+                for (int q = p + 1; q < BS; ++q) acc += A[p][q] * v[q];
+                r[p] = acc;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < BS; ++p) out[p] = r[p];
+    };
+    // out = C_i v
+    auto mulC = [&](int i, const T (&v)[BS], T (&out)[BS]) {
+        T r[BS];
+        if constexpr (BS == 2) {
+            r[0] = v[0] + tb * v[1];
+            r[1] = v[1] + aw[i + 2] * v[0];
+        } else {
+            T C[BS][BS];
+            blockC(i, C);
+#pragma unroll
+            for (int p = 0; p < BS; ++p) {
+                T acc = C[p][0] * v[0];
+#pragma unroll
+                for (int q = 1; q <= p; ++q) acc += C[p][q] * v[q];
+                r[p] = acc;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < BS; ++p) out[p] = r[p];
+    };
+    // out = -Si t
+    auto neg_si = [&](const T (&Si)[BS][BS], const T (&t)[BS], T (&out)[BS]) {
+        T r[BS];
 #pragma unroll
         for (int p = 0; p < BS; ++p) {
-            T acc = T(0);
+            T acc = Si[p][0] * t[0];
 #pragma unroll
-            for (int q = 0; q < BS; ++q) acc += M[p][q] * v[q];
-            t[p] = acc;
+            for (int q = 1; q < BS; ++q) acc += Si[p][q] * t[q];
+            r[p] = -acc;
         }
 #pragma unroll
-        for (int p = 0; p < BS; ++p) {
-            T acc = T(0);
-#pragma unroll
-            for (int q = 0; q < BS; ++q) acc -= Si[p][q] * t[q];
-            out[p] = acc;
-        }
+        for (int p = 0; p < BS; ++p) out[p] = r[p];
     };
 
     // ---- factorisation and local forward pass ----
@@ -1155,18 +1182,26 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
             if (i == 0) {
                 load_blk<T, BS>(sR + c * B2, S);
             } else {
-                T A[BS][BS], B[BS][BS];
-                blockA(i, A);
-                blockB(i, B);
+                // S_i = B_i - A_i G_{i-1}
+                if constexpr (BS == 2) {
+                    S[0][0] = T(4) - G[0][0] + tb * G[1][0];
+                    S[0][1] = tb * G[1][1] - G[0][1];
+                    S[1][0] = aw[i] * G[0][0] - G[1][0];
+                    S[1][1] = T(4) - G[1][1] + aw[i] * G[0][1];
+                } else {
+                    T A[BS][BS], B[BS][BS];
+                    blockA(i, A);
+                    blockB(i, B);
 #pragma unroll
-                for (int p = 0; p < BS; ++p)
+                    for (int p = 0; p < BS; ++p)
 #pragma unroll
-                    for (int q = 0; q < BS; ++q) {
-                        T acc = B[p][q];
+                        for (int q = 0; q < BS; ++q) {
+                            T acc = B[p][q];
 #pragma unroll
-                        for (int k = 0; k < BS; ++k) acc -= A[p][k] * G[k][q];
-                        S[p][q] = acc;
-                    }
+                            for (int k = p; k < BS; ++k) acc -= A[p][k] * G[k][q];
+                            S[p][q] = acc;
+                        }
+                }
                 if (i == MM - 1 && is_tail) {
 #pragma unroll
                     for (int p = 0; p < BS; ++p)
@@ -1175,10 +1210,14 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 }
             }
             fac_inv<T, BS>(S, Si[i]);
+            // y_i = Si_i (r_i - A_i y_{i-1})
             T t[BS];
             if (i == 0) {
 #pragma unroll
                 for (int p = 0; p < BS; ++p) t[p] = Y[0][p];
+            } else if constexpr (BS == 2) {
+                t[0] = Y[i][0] - Y[i - 1][0] + tb * Y[i - 1][1];
+                t[1] = Y[i][1] - Y[i - 1][1] + aw[i] * Y[i - 1][0];
             } else {
                 T A[BS][BS];
                 blockA(i, A);
@@ -1186,21 +1225,37 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
                 for (int p = 0; p < BS; ++p) {
                     T acc = Y[i][p];
 #pragma unroll
-                    for (int q = 0; q < BS; ++q) acc -= A[p][q] * Y[i - 1][q];
+                    for (int q = p; q < BS; ++q) acc -= A[p][q] * Y[i - 1][q];
                     t[p] = acc;
                 }
             }
 #pragma unroll
             for (int p = 0; p < BS; ++p) {
-                T acc = T(0);
+                T acc = Si[i][p][0] * t[0];
 #pragma unroll
-                for (int q = 0; q < BS; ++q) acc += Si[i][p][q] * t[q];
+                for (int q = 1; q < BS; ++q) acc += Si[i][p][q] * t[q];
                 Y[i][p] = acc;
             }
-            if (i + 1 < MM) {
-                T C[BS][BS];
-                blockC(i, C);
-                f_mm<T, BS>(Si[i], C, G);
+            if (i + 1 < MM) {  // G_i = Si_i C_i
+                if constexpr (BS == 2) {
+                    const T a2 = aw[i + 2];
+                    G[0][0] = Si[i][0][0] + Si[i][0][1] * a2;
+                    G[0][1] = Si[i][0][0] * tb + Si[i][0][1];
+                    G[1][0] = Si[i][1][0] + Si[i][1][1] * a2;
+                    G[1][1] = Si[i][1][0] * tb + Si[i][1][1];
+                } else {
+                    T C[BS][BS];
+                    blockC(i, C);
+#pragma unroll
+                    for (int p = 0; p < BS; ++p)
+#pragma unroll
+                        for (int q = 0; q < BS; ++q) {
+                            T acc = Si[i][p][q] * C[q][q];
+#pragma unroll
+                            for (int k = q + 1; k < BS; ++k) acc += Si[i][p][k] * C[k][q];
+                            G[p][q] = acc;
+                        }
+                }
             }
         }
     }
@@ -1254,21 +1309,21 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
 #pragma unroll
         for (int p = 0; p < BS; ++p) dl[p] = yin[p];
 #pragma unroll
-        for (int i = 0; i < MM; ++i) {
-            T A[BS][BS];
-            blockA(i, A);
-            neg_si_mv(Si[i], A, dl, dl);
+        for (int i = 0; i < MM; ++i) {  // d_i = -Si_i A_i d_{i-1}
+            T t[BS];
+            mulA(i, dl, t);
+            neg_si(Si[i], t, dl);
 #pragma unroll
             for (int p = 0; p < BS; ++p) Y[i][p] += dl[p];
         }
         // local backward pass (x = 0 after the chunk): x_i = y_i - Si_i (C_i x_{i+1})
 #pragma unroll
         for (int i = MM - 2; i >= 0; --i) {
-            T C[BS][BS], t[BS];
-            blockC(i, C);
-            neg_si_mv(Si[i], C, Y[i + 1], t);
+            T t[BS], u[BS];
+            mulC(i, Y[i + 1], t);
+            neg_si(Si[i], t, u);
 #pragma unroll
-            for (int p = 0; p < BS; ++p) Y[i][p] += t[p];
+            for (int p = 0; p < BS; ++p) Y[i][p] += u[p];
         }
     }
 
@@ -1297,10 +1352,10 @@ __device__ __forceinline__ void fac_group(unsigned char *stage_raw, int natural,
 #pragma unroll
         for (int p = 0; p < BS; ++p) ep[p] = xin[p];
 #pragma unroll
-        for (int i = MM - 1; i >= 0; --i) {
-            T C[BS][BS];
-            blockC(i, C);
-            neg_si_mv(Si[i], C, ep, ep);
+        for (int i = MM - 1; i >= 0; --i) {  // e_i = -Si_i C_i e_{i+1}
+            T t[BS];
+            mulC(i, ep, t);
+            neg_si(Si[i], t, ep);
 #pragma unroll
             for (int p = 0; p < BS; ++p) Y[i][p] += ep[p];
         }
