@@ -65,10 +65,14 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 // Geometry of a line for the factored solver.
 // ---------------------------------------------------------------------------------------
 // Blocks per chunk: CFD 9 (an odd stride between the chunks' shared-memory windows keeps
-// their loads free of bank conflicts); MFD 2 for lines up to 2 kFacMaxT blocks, else 3.
+// their loads free of bank conflicts); MFD 3 (a chunk's record, S, F and H of 3 x 3, then costs
+// 12 bytes per cell in FP32; two-block chunks cost 18 and ran a batch of 128-1024-cell lines 4 %
+// slower), and 2 for lines of at most kFacMfdShort cells, whose end regions would not fit their
+// tables with the remainder of three-block chunks.
+constexpr int kFacMfdShort = 16;
 __host__ __device__ inline int fac_mm(int method, int N) {
     if (method == kCFD) return 9;
-    return line_shape(kMFD, N).nb <= 2 * kFacMaxT ? 2 : 3;
+    return N <= kFacMfdShort ? 2 : 3;
 }
 // Threads a whole line needs (see fac_geom): a power of two up to 32, else a multiple of 32.
 __host__ __device__ inline int fac_geom_T(int method, int N) {
