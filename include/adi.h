@@ -134,12 +134,13 @@ int adi_autotune(adi_handle sim, int trials, int force, int *chosen, double *ms_
  * adi_set_launch / adi_get_launch -- launch parameters of the factored line solver (the paper
  * has no counterpart: GPU launch shape).  lines_per_cta caps the lines one CTA solves together
  * (0: as many as its threads and shared memory take); ring_depth caps the staged groups in
- * flight per CTA (2 or 0: prefetch the next group while solving one, 1: no prefetch).  The
- * results do not change (every line is solved by the same arithmetic), only the time.  When
- * the factored solver is the fastest, adi_autotune also times every lines_per_cta from the
- * automatic count halved down to 1 with both ring depths, keeps the fastest and caches it with
- * the solver choice; adi_get_launch reports the current caps (0 = automatic).
- * Errors: ADI_EINVAL, ADI_EBUSY inside a batch.
+ * flight per CTA (0: as many as shared memory takes, at most 3; 1: no prefetch; 2: prefetch
+ * the next group while solving one; 3: the next two).  The results do not change (every line
+ * is solved by the same arithmetic), only the time.  When the factored solver is the fastest,
+ * adi_autotune also times every lines_per_cta from the automatic count halved down to 1 with
+ * the ring depths 0, 1 and 2, keeps the fastest and caches it with the solver choice;
+ * adi_get_launch reports the current caps (0 = automatic).
+ * Errors: ADI_EINVAL (ring_depth outside 0..3), ADI_EBUSY inside a batch.
  */
 int adi_set_launch(adi_handle sim, int lines_per_cta, int ring_depth);
 int adi_get_launch(adi_handle sim, int *lines_per_cta, int *ring_depth);

@@ -185,7 +185,7 @@ struct Plan {
     DevBuf fgroups[2][kFacVariants];
     int nfgroups[2][kFacVariants] = {};
     size_t fstage[2][kFacVariants] = {};  // shared memory of one pipeline stage
-    int fstages[2][kFacVariants] = {};    // pipeline depth (2 = prefetch)
+    int fstages[2][kFacVariants] = {};    // staged groups in flight per CTA (1 to 3)
     int fgrid[2][kFacVariants] = {};      // persistent CTAs
     int fring[2][kFacVariants] = {};      // ring-depth cap of the launch (0: none)
     // carried-pressure transposes after each stage, one array per member: [dir]
@@ -657,7 +657,7 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
         }
         for (int v = 0; v < kFacVariants && !rc; ++v) {
             p.nfgroups[dir][v] = (int)fgr[dir][v].size();
-            p.fstages[dir][v] = fac_stages_for(p.fstage[dir][v], esz);
+            p.fstages[dir][v] = fac_stages_for(p.fstage[dir][v], esz, (v == 0 || v == 3) ? ADI_CFD : ADI_MFD);
             if (p.fring[dir][v] > 0) p.fstages[dir][v] = std::min(p.fstages[dir][v], p.fring[dir][v]);
             p.fgrid[dir][v] = std::min(p.nfgroups[dir][v], sm_count());
             if (p.nfgroups[dir][v] && !p.fstages[dir][v]) { rc = ADI_ENOTSUP; break; }
@@ -1343,7 +1343,8 @@ int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_pe
             if (res.solver < 0 || ms < best) { best = ms; res.solver = sv; }
         }
         // the factored solver's launch parameters: lines per CTA (the automatic count, then
-        // halved down to one) and the staging ring depth (2: prefetch, 1: none)
+        // halved down to one) and the staging ring depth (automatic: as many groups in flight
+        // as shared memory takes, up to three; then capped at 1 and at 2)
         if (!rc && res.solver == ADI_SOLVER_FACTORED) {
             rc = adi_set_solver(s, ADI_SOLVER_FACTORED);
             const int nl0 = std::max(fac_split_line(s->g.method, s->g.nx) ? 1 : fac_lines_per_cta(s->g.method, s->g.nx, s->esz),
@@ -1352,7 +1353,7 @@ int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_pe
             for (int c = nl0 / 2; c >= 1; c /= 2) caps.push_back(c);
             res.ms_launch = res.ms[ADI_SOLVER_FACTORED];
             for (size_t ci = 0; ci < caps.size() && !rc; ++ci)
-                for (int ring = 0; ring <= 1 && !rc; ++ring) {
+                for (int ring = 0; ring <= 2 && !rc; ++ring) {
                     if (ci == 0 && ring == 0) continue;  // the automatic choice, timed above
                     s->fac_nl_cap = caps[ci];
                     s->fac_ring_cap = ring;
@@ -1387,13 +1388,13 @@ int adi_autotune(adi_handle s, int trials, int force, int *chosen, double *ms_pe
 }
 
 int adi_set_launch(adi_handle s, int lines_per_cta, int ring_depth) {
-    if (!s || lines_per_cta < 0 || ring_depth < 0 || ring_depth > 2) return ADI_EINVAL;
+    if (!s || lines_per_cta < 0 || ring_depth < 0 || ring_depth > 3) return ADI_EINVAL;
     if (s->sticky) return s->sticky;
     if (s->in_batch) return ADI_EBUSY;
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->sticky = cuda_status(e);
     s->fac_nl_cap = lines_per_cta;
-    s->fac_ring_cap = ring_depth == 2 ? 0 : ring_depth;
+    s->fac_ring_cap = ring_depth;
     int rc = plan_build(s->plan, std::vector<adi_sim *>{s}, s->stream);
     s->plan_base = s->parity;
     if (rc) s->sticky = rc;

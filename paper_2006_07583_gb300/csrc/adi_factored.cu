@@ -48,12 +48,14 @@ constexpr int kFacThreads = 512;              // threads per CTA: 15 compute war
 constexpr int kFacWorkers = kFacThreads - 32; // threads that solve lines
 constexpr int kFacMaxT = kFacWorkers;         // chunks (threads) per line at most
 constexpr size_t kFacSmemLimit = 227 * 1024;  // shared memory per CTA
-constexpr size_t kFacStaticBase = 4096;       // reserve for the kernel's other static shared memory
+constexpr size_t kFacStaticBase = 2048;       // reserve for the kernel's other static shared memory
+constexpr int kFacMaxStages = 3;              // staged groups in flight per CTA at most
 constexpr int kFacWs = 1024;                  // FP64 workspace of the precompute, per line
-// Static shared memory of the kernel for element size esz: the scan buffers (chunk offsets,
-// two arrays for FP32, one for FP64) plus the rest.
-__host__ __device__ inline size_t fac_static_smem(size_t esz) {
-    return kFacStaticBase + (size_t)kFacThreads * 3 * (esz == 4 ? 2 : 1) * esz;
+// Static shared memory of the kernel for element size esz and block size bs, an upper bound:
+// the scan buffers (chunk offsets, two arrays for FP32, one for FP64) plus the rest (checked
+// against the compiled kernel before its first launch).
+__host__ __device__ inline size_t fac_static_smem(size_t esz, int bs) {
+    return kFacStaticBase + (size_t)kFacThreads * bs * (esz == 4 ? 2 : 1) * esz;
 }
 
 // One rounding for a*b + c, written out so that the compiler's contraction choices cannot make
@@ -164,9 +166,10 @@ size_t fac_stage_bytes(int method, int N, int nl, size_t esz) {
     size_t b = fac_head_bytes(nl) + (size_t)nl * fac_line_elems(fac_geom(method, N)) * esz;
     return (b + 127) & ~(size_t)127;
 }
-int fac_stages_for(size_t stage_bytes, size_t esz) {
-    if (2 * stage_bytes + fac_static_smem(esz) <= kFacSmemLimit) return 2;
-    if (stage_bytes + fac_static_smem(esz) <= kFacSmemLimit) return 1;
+int fac_stages_for(size_t stage_bytes, size_t esz, int method) {
+    const size_t st = fac_static_smem(esz, method == kCFD ? 2 : 3);
+    for (int k = kFacMaxStages; k >= 1; --k)
+        if ((size_t)k * stage_bytes + st <= kFacSmemLimit) return k;
     return 0;
 }
 // Lines per CTA: as many as the CTA's threads cover, fewer where a two-stage ring of them
@@ -174,7 +177,7 @@ int fac_stages_for(size_t stage_bytes, size_t esz) {
 int fac_lines_per_cta(int method, int N, size_t esz) {
     const int T = fac_geom(method, N).T;
     int nl = T >= kFacWorkers ? 1 : kFacWorkers / T;
-    while (nl > 1 && fac_stages_for(fac_stage_bytes(method, N, nl, esz), esz) < 2) --nl;
+    while (nl > 1 && fac_stages_for(fac_stage_bytes(method, N, nl, esz), esz, method) < 2) --nl;
     return nl;
 }
 bool fac_split_line(int method, int N) { return fac_geom(method, N).T > kFacMaxT; }
@@ -187,7 +190,7 @@ bool fac_supported(int method, int N, size_t esz) {
         size_t sb = 0;
         return fac_split_groups(method, N, 0, kFacSplitMaxHalo, 1.0, 1.0, esz, tmp, &sb) > 0;
     }
-    return fac_stages_for(fac_stage_bytes(method, N, 1, esz), esz) > 0;
+    return fac_stages_for(fac_stage_bytes(method, N, 1, esz), esz, method) > 0;
 }
 size_t fac_words(int method, int N) { return (size_t)fac_rec(fac_geom(method, N)); }
 int fac_chunks(int method, int N) { return fac_geom(method, N).T; }
@@ -274,7 +277,7 @@ int fac_split_groups(int method, int N, int first, int halo, double inv_h, doubl
         if (sb > smax) smax = sb;
     }
     *stage_bytes = smax;
-    return fac_stages_for(smax, esz) > 0 ? K : 0;
+    return fac_stages_for(smax, esz, method) > 0 ? K : 0;
 }
 // Table offsets of an end region, as compile-time functions of the block size (fac_e_*).
 template <int BS>
@@ -1600,27 +1603,26 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
                            int natural, unsigned stage_bytes, int stages, int *fault) {
     extern __shared__ __align__(128) unsigned char fac_smem[];
     __shared__ ScanSmem<T, BS> ssm;
-    __shared__ __align__(8) unsigned long long full[2], empty[2];
+    __shared__ __align__(8) unsigned long long full[kFacMaxStages], empty[kFacMaxStages];
     // chunk offsets of the windowed scans: forward and backward buffers for FP32, one for FP64
     constexpr int kBufs = sizeof(T) == 4 ? 2 : 1;
     __shared__ T offs[kBufs][kFacThreads * BS];
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kFacMaxStages; ++k) {
             mbar_init(&full[k], 1);
             mbar_init(&empty[k], kFacWorkers / 32);
         }
         mbar_fence_init();
     }
     __syncthreads();
-    const bool two = stages == 2;
+    // the it-th group of this CTA goes to stage it % stages, as that stage's use-th group
     if (tid >= kFacWorkers) {  // the staging warp
         if (lane == 0) {
-            int last[2] = {-1, -1};
-            int it = 0;
-            for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x, ++it) {
-                const int st = two ? (it & 1) : 0;
-                const int use = two ? (it >> 1) : it;
+            int last[kFacMaxStages];
+            for (int k = 0; k < kFacMaxStages; ++k) last[k] = -1;
+            int st = 0, use = 0;
+            for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
                 unsigned char *stage = fac_smem + (size_t)st * stage_bytes;
                 if (use > 0) {
                     // the previous group of this stage is solved: write its outputs, then refill.
@@ -1633,10 +1635,11 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
                 }
                 fac_issue<T, BS, SPLIT>(descs, groups + gi, stage, &full[st]);
                 last[st] = use;
+                if (++st == stages) { st = 0; ++use; }
             }
             // the last groups of each stage: wait until solved and until their copies have
             // landed (no bulk copy into this CTA's shared memory may outlive it), write outputs
-            for (int k = 0; k < 2; ++k)
+            for (int k = 0; k < stages; ++k)
                 if (last[k] >= 0) {
                     if (!mbar_wait(&empty[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
                     if (!mbar_wait(&full[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
@@ -1647,14 +1650,13 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
         }
         return;
     }
-    int it = 0;
-    for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x, ++it) {
-        const int st = two ? (it & 1) : 0;
-        const int use = two ? (it >> 1) : it;
+    int st = 0, use = 0;
+    for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
         if (!mbar_wait(&full[st], (unsigned)(use & 1))) atomicExch(fault, 1);
         fac_group<T, BS, MM, SPLIT>(fac_smem + (size_t)st * stage_bytes, natural, ssm, offs[0], offs[kBufs - 1]);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
+        if (++st == stages) { st = 0; ++use; }
     }
 }
 
@@ -1669,6 +1671,13 @@ template <typename T, int BS, int MM, bool SPLIT>
 cudaError_t launch_fac_inst(const LineDesc<T> *d, const FacGroup *groups, int ngroups, size_t stage_bytes, int stages,
                             int grid, int natural, int *fault, cudaStream_t s) {
     auto kern = line_solve_factored_kernel<T, BS, MM, SPLIT>;
+    // the host sizes the ring with fac_static_smem, an upper bound of the kernel's own static
+    // shared memory: check it against the compiled kernel once
+    static const bool static_ok = [&] {
+        cudaFuncAttributes a{};
+        return cudaFuncGetAttributes(&a, kern) == cudaSuccess && a.sharedSizeBytes <= fac_static_smem(sizeof(T), BS);
+    }();
+    if (!static_ok) return cudaErrorInvalidConfiguration;
     const size_t dyn = (size_t)stages * stage_bytes;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
@@ -1682,7 +1691,7 @@ cudaError_t launch_line_solve_factored(const LineDesc<T> *d, const FacGroup *gro
                                        cudaStream_t s) {
     if (ngroups <= 0) return cudaSuccess;
     if (grid > ngroups) grid = ngroups;
-    if (stages != 1 && stages != 2) return cudaErrorInvalidValue;
+    if (stages < 1 || stages > kFacMaxStages) return cudaErrorInvalidValue;
     switch (variant) {
     case 0: return launch_fac_inst<T, 2, 9, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, fault, s);
     case 1: return launch_fac_inst<T, 3, 2, false>(d, groups, ngroups, stage_bytes, stages, grid, natural, fault, s);

@@ -144,7 +144,7 @@ int fac_variant(int method, int N);      // compiled kernel instance: 0 CFD, 1-2
 constexpr int kFacVariants = 5;
 int fac_lines_per_cta(int method, int N, size_t esz);
 size_t fac_stage_bytes(int method, int N, int nl, size_t esz);  // shared memory of one stage
-int fac_stages_for(size_t stage_bytes, size_t esz);  // 2 (prefetch), 1, or 0 (does not fit)
+int fac_stages_for(size_t stage_bytes, size_t esz, int method);  // groups in flight that fit: 3, 2, 1 or 0
 size_t fac_ws_doubles();                 // FP64 workspace per line of the precompute
 // status[0]: set when a line system is singular; status[1]: atomic max of the lines' scan reach
 template <typename T>

@@ -27,7 +27,7 @@ int main() {
                     const int W = fac_win(method), per = method == 0 ? MM : 3 * MM;
                     const int pg = fac_part(g), es = fac_e_stride(g), recg = fac_rec(g);
                     std::vector<int> pown(pl + 1, 0), vown(N + 1, 0), chunkown(g.tact, 0);
-                    CHECK(2 * sb + fac_static_smem(esz) <= kFacSmemLimit || sb + fac_static_smem(esz) <= kFacSmemLimit, "smem");
+                    CHECK(sb + fac_static_smem(esz, g.bs) <= kFacSmemLimit, "smem");
                     for (int i = 0; i < K; ++i) {
                         const FacGroup &r = sub[i];
                         const bool head = r.own & kFacOwnHead, tail = r.own & kFacOwnTail;
@@ -103,14 +103,14 @@ int main() {
                     const int nl = fac_lines_per_cta(method, N, esz);
                     CHECK(nl >= 1 && nl * g.T <= kFacMaxT, "lines per CTA N %d", N);
                     const size_t sb = fac_stage_bytes(method, N, nl, esz);
-                    CHECK(fac_stages_for(sb, esz) >= 1, "stage N %d", N);
-                    CHECK((size_t)fac_stages_for(sb, esz) * sb + fac_static_smem(esz) <= kFacSmemLimit, "smem N %d", N);
+                    CHECK(fac_stages_for(sb, esz, method) >= 1, "stage N %d", N);
+                    CHECK((size_t)fac_stages_for(sb, esz, method) * sb + fac_static_smem(esz, g.bs) <= kFacSmemLimit, "smem N %d", N);
                 } else {
                     FacGroup sub[kFacMaxSplit];
                     size_t sb = 0;
                     const int K = fac_split_groups(method, N, 0, kFacSplitMaxHalo, 1.0, 1.0, esz, sub, &sb);
                     CHECK(K >= 2, "split N %d", N);
-                    CHECK((size_t)fac_stages_for(sb, esz) * sb + fac_static_smem(esz) <= kFacSmemLimit, "split smem N %d", N);
+                    CHECK((size_t)fac_stages_for(sb, esz, method) * sb + fac_static_smem(esz, g.bs) <= kFacSmemLimit, "split smem N %d", N);
                 }
             }
     printf("bad %d\n", bad);
