@@ -63,11 +63,15 @@ def test_autotune_rejects_bad_arguments(adi):
     s = _sim(adi, sp, 0)
     with pytest.raises(adi.AdiError):
         s.autotune(trials=0)
+    with pytest.raises(adi.AdiError):
+        s.set_launch(0, 4)  # at most three groups in flight
     s.close()
 
 
+# (CFD, 4096, 48) in FP32: its 4096-cell x-lines are the ones whose stage fits three times
 @pytest.mark.parametrize("method,nx,ny,prec", [(wl.CFD, 300, 220, 0), (wl.MFD, 260, 197, 0),
-                                               (wl.CFD, 130, 700, 1), (wl.MFD, 1024, 128, 0)])
+                                               (wl.CFD, 130, 700, 1), (wl.MFD, 1024, 128, 0),
+                                               (wl.CFD, 4096, 48, 0)])
 def test_launch_parameters_leave_results_unchanged(adi, method, nx, ny, prec):
     """Every lines-per-CTA cap and ring depth of the factored solver gives the same numbers as
     the automatic launch: each line is solved by the same arithmetic whatever its group."""
