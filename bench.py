@@ -645,7 +645,7 @@ def serving_leg(adi, n_req, with_fp64=True):
     return out
 
 
-def tune_leg(adi, sides=(256, 1024, 4096)):
+def tune_leg(adi, sides=(256, 1024, 4096, 8192)):
     """adi_autotune on single FP32 seismic simulations per size class: ms per step of every
     solver with the automatic launch, and of the factored solver with the launch parameters the
     tuner keeps (lines per CTA cap, ring depth cap; 0 = automatic)."""

@@ -789,12 +789,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 
 __host__ __device__ inline unsigned round16(unsigned b) { return (b + 15u) & ~15u; }
 
-// Bulk copies (shared -> global) of the staged outputs of a solved group, issued by the staging
-// lane once the compute warps have released the stage; each line's pressure output (in place of
-// its pressure line) and v' (in place of alpha).  Lines shorter than a warp were stored
-// directly by the compute warps.  Returns once the copies have read the stage.
+// Bulk copies (shared -> global) of the staged outputs of a solved group, issued by the lanes
+// of the staging warp once the compute warps have released the stage (lane k takes lines k,
+// k + 32, ...); each line's pressure output (in place of its pressure line) and v' (in place
+// of alpha).  Lines shorter than a warp were stored directly by the compute warps.  Returns
+// once this lane's copies have read the stage.
 template <typename T>
-__device__ void fac_store_outputs(const unsigned char *stage) {
+__device__ void fac_store_outputs(const unsigned char *stage, int lane) {
     const FacGroup &gr = *(const FacGroup *)stage;
     if (gr.T < 32) return;
     const LineDesc<T> *descs = (const LineDesc<T> *)(stage + kFacGroupBytes);
@@ -803,7 +804,7 @@ __device__ void fac_store_outputs(const unsigned char *stage) {
     // 16 bytes only at the line's end (inside the padded line)
     const unsigned pbytes = round16((unsigned)(gr.sp1 - gr.sp0) * (unsigned)sizeof(T));
     const unsigned vbytes = round16((unsigned)(gr.sv1 - gr.sv0) * (unsigned)sizeof(T));
-    for (int l = 0; l < gr.nl; ++l) {
+    for (int l = lane; l < gr.nl; l += 32) {
         const T *sp = base + (size_t)l * gr.ls - gr.lo;  // staged element k at sp[k]
         if (pbytes)
             asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(descs[l].po + gr.sp0),
@@ -818,16 +819,19 @@ __device__ void fac_store_outputs(const unsigned char *stage) {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-// Thread 0: stage one line group (descriptors, then per line the pressure, velocity and alpha
-// lines and the record) into shared memory.  A sub-line of a split line stages its span of the
-// three lines and, of the record, its chunks' S, F and H parts, the end tables it holds and the
-// reach.  Every source starts on a 16-byte boundary (padded leading dimensions; spans start at
-// multiples of four elements; record parts are padded to four elements and sub-line ranges
-// start at multiples of four chunks) and the copies, rounded up to 16 bytes, stay inside the
-// padded line or the record.
+// The staging warp: stage one line group (descriptors, then per line the pressure, velocity
+// and alpha lines and the record) into shared memory.  Lane 0 announces the group's bytes on the
+// stage's "full" barrier (its only arrival) and copies the header and the descriptors; lane k
+// reads the descriptors of lines k, k + 32, ... from global memory and issues their copies, so
+// that a group of many short lines costs one round trip for its descriptors, not one per line.
+// A sub-line of a split line stages its span of the three lines and, of the record, its chunks'
+// S, F and H parts, the end tables it holds and the reach.  Every source starts on a 16-byte
+// boundary (padded leading dimensions; spans start at multiples of four elements; record parts
+// are padded to four elements and sub-line ranges start at multiples of four chunks) and the
+// copies, rounded up to 16 bytes, stay inside the padded line or the record.
 template <typename T, int BS, bool SPLIT>
 __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, const FacGroup *gp, unsigned char *stage,
-                          unsigned long long *bar) {
+                          unsigned long long *bar, int lane) {
     const FacGroup &gr = *gp;
     const int Lp = gr.lp, lo = SPLIT ? gr.lo : 0;
     const unsigned bp = round16((unsigned)gr.pn * (unsigned)sizeof(T));
@@ -835,11 +839,14 @@ __device__ void fac_issue(const LineDesc<T> *__restrict__ descs, const FacGroup 
     const unsigned br = (unsigned)(gr.info + 4) * (unsigned)sizeof(T);  // the staged record
     const unsigned bd = (unsigned)(gr.nl * kDescBytes);
     const unsigned bg = (unsigned)sizeof(FacGroup);
-    mbar_expect_tx(bar, bg + bd + (unsigned)gr.nl * (2 * bp + bv + br));
-    bulk_to_smem(stage, gp, bg, bar);
-    bulk_to_smem(stage + kFacGroupBytes, descs + gr.first, bd, bar);
+    if (lane == 0) {
+        mbar_expect_tx(bar, bg + bd + (unsigned)gr.nl * (2 * bp + bv + br));
+        bulk_to_smem(stage, gp, bg, bar);
+        bulk_to_smem(stage + kFacGroupBytes, descs + gr.first, bd, bar);
+    }
+    __syncwarp();  // the group's bytes are announced before any line copy is issued
     T *base = (T *)(stage + fac_head_bytes(gr.nl));
-    for (int l = 0; l < gr.nl; ++l) {
+    for (int l = lane; l < gr.nl; l += 32) {
         const LineDesc<T> &d = descs[gr.first + l];
         T *ln = base + (size_t)l * gr.ls;
         bulk_to_smem(ln, d.p + lo, bp, bar);
@@ -1617,37 +1624,36 @@ line_solve_factored_kernel(const LineDesc<T> *__restrict__ descs, const FacGroup
     }
     __syncthreads();
     // the it-th group of this CTA goes to stage it % stages, as that stage's use-th group
-    if (tid >= kFacWorkers) {  // the staging warp
-        if (lane == 0) {
-            int last[kFacMaxStages];
-            for (int k = 0; k < kFacMaxStages; ++k) last[k] = -1;
-            int st = 0, use = 0;
-            for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
-                unsigned char *stage = fac_smem + (size_t)st * stage_bytes;
-                if (use > 0) {
-                    // the previous group of this stage is solved: write its outputs, then refill.
-                    // The copies that filled it have landed (the compute warps waited for them);
-                    // if a compute warp's wait ran out they may not have, so this lane waits for
-                    // them itself before it copies anything into the stage again.
-                    if (!mbar_wait(&empty[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
-                    if (!mbar_wait(&full[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
-                    fac_store_outputs<T>(stage);
-                }
-                fac_issue<T, BS, SPLIT>(descs, groups + gi, stage, &full[st]);
-                last[st] = use;
-                if (++st == stages) { st = 0; ++use; }
+    if (tid >= kFacWorkers) {  // the staging warp; every lane runs the same loop
+        int last[kFacMaxStages];
+        for (int k = 0; k < kFacMaxStages; ++k) last[k] = -1;
+        int st = 0, use = 0;
+        for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
+            unsigned char *stage = fac_smem + (size_t)st * stage_bytes;
+            if (use > 0) {
+                // the previous group of this stage is solved: write its outputs, then refill.
+                // The copies that filled it have landed (the compute warps waited for them);
+                // if a compute warp's wait ran out they may not have, so every lane waits for
+                // them itself before it copies anything into the stage again.
+                if (!mbar_wait(&empty[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
+                if (!mbar_wait(&full[st], (unsigned)((use - 1) & 1))) atomicExch(fault, 1);
+                fac_store_outputs<T>(stage, lane);
+                __syncwarp();  // every lane's output copies have read the stage
             }
-            // the last groups of each stage: wait until solved and until their copies have
-            // landed (no bulk copy into this CTA's shared memory may outlive it), write outputs
-            for (int k = 0; k < stages; ++k)
-                if (last[k] >= 0) {
-                    if (!mbar_wait(&empty[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
-                    if (!mbar_wait(&full[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
-                    fac_store_outputs<T>(fac_smem + (size_t)k * stage_bytes);
-                }
-            // global visibility of the output copies before the CTA ends
-            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            fac_issue<T, BS, SPLIT>(descs, groups + gi, stage, &full[st], lane);
+            last[st] = use;
+            if (++st == stages) { st = 0; ++use; }
         }
+        // the last groups of each stage: wait until solved and until their copies have
+        // landed (no bulk copy into this CTA's shared memory may outlive it), write outputs
+        for (int k = 0; k < stages; ++k)
+            if (last[k] >= 0) {
+                if (!mbar_wait(&empty[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
+                if (!mbar_wait(&full[k], (unsigned)(last[k] & 1))) atomicExch(fault, 1);
+                fac_store_outputs<T>(fac_smem + (size_t)k * stage_bytes, lane);
+            }
+        // global visibility of this lane's output copies before the CTA ends
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
         return;
     }
     int st = 0, use = 0;
