@@ -59,6 +59,10 @@ def parse():
                     help="skip the FP64 one-at-a-time comparator of the serving leg")
     ap.add_argument("--no-batch256", action="store_true", help="skip the 256-simulation batch leg")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner leg")
+    ap.add_argument("--batch-only", type=int, default=0, metavar="NSIMS",
+                    help="run only the config-3 batch leg with NSIMS simulations (half CFD, half MFD) "
+                         "and print its JSON (the profiling case of the many-short-lines launches)")
+    ap.add_argument("--batch-steps", type=int, default=100, help="graph-captured steps of the batch leg")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of the main batched leg (fp64: the profiling case of the FP64 kernels)")
     ap.add_argument("--solver", default="default", choices=["default", "line", "chunked", "factored"],
@@ -293,6 +297,13 @@ def main():
     import torch
 
     torch.cuda.set_device(local)
+    if args.batch_only:
+        from paper_2006_07583_gb300 import adi
+
+        adi.lib()
+        peak, _ = measured_peaks()
+        emit(batch256_leg(adi, torch, peak, steps=args.batch_steps, n_sims=args.batch_only))
+        return 0
     if ws > 1:
         import torch.distributed as dist
 
@@ -396,7 +407,7 @@ def main():
     if rank == 0 and not args.no_fp64:
         out["fp64_factored"] = fp64_factored_leg(adi, torch, args.side, peak)
     if rank == 0 and not args.no_batch256:
-        out["batch256"] = batch256_leg(adi, torch, peak)
+        out["batch256"] = batch256_leg(adi, torch, peak, steps=args.batch_steps)
     if rank == 0 and not args.no_serve:
         out["serving"] = serving_leg(adi, args.serve_requests, not args.no_serve_fp64)
     if rank == 0 and not args.no_tune:
@@ -673,14 +684,15 @@ def tune_leg(adi, sides=(256, 1024, 4096, 8192)):
     return out
 
 
-def batch256_leg(adi, torch, peak, steps=100):
+def batch256_leg(adi, torch, peak, steps=100, n_sims=256):
     """Config 3: 256 independent simulations (128 CFD + 128 MFD), sides uniform in [128, 1024],
     seeded layered media, Ricker sources, FP32, batched.  `steps` graph-captured steps after
     warm-up, CUDA events on the batch's stream; then a few half-step pairs with events around
-    the solve launches for the kernels' roofline (20 B per point and stage)."""
+    the solve launches for the kernels' roofline (20 B per point and stage).  A smaller n_sims
+    draws a smaller batch the same way, half CFD and half MFD (the profiling case)."""
     from paper_2006_07583_gb300 import workloads as wl
 
-    specs = wl.batch_specs(256, 128, 1024, steps, seed=2)
+    specs = wl.batch_specs(n_sims, 128, 1024, steps, seed=2)
     sims = []
     for sp in specs:
         s = adi.Sim(sp.method, sp.nx, sp.ny, sp.h, sp.dt, sp.c, precision=adi.ADI_FP32)
@@ -709,8 +721,9 @@ def batch256_leg(adi, torch, peak, steps=100):
     b.close()
     for s in sims:
         s.close()
-    return {"workload": "config 3: 256 sims (128 CFD + 128 MFD), sides uniform 128-1024, FP32, "
-                        "one batch, graph-captured steps", "value": pts / (ms / 1e3), "unit": UNIT,
+    return {"workload": "config 3: %d sims (%d CFD + %d MFD), sides uniform 128-1024, FP32, "
+                        "one batch, graph-captured steps" % (n_sims, n_sims // 2, n_sims - n_sims // 2),
+            "value": pts / (ms / 1e3), "unit": UNIT,
             "ms_per_step": ms, "steps": steps, "points": pts,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "solve_ms": solve_ms}}
