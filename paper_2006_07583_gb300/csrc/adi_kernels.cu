@@ -392,45 +392,68 @@ __device__ __forceinline__ T prologue_src(const LineDesc<T> &d) {
 template <typename T>
 __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, int nlines, int N, int method,
                                         T *scratch, long long st) {
-    const int line = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    if (line >= nlines || j > N + 1) return;
-    const LineDesc<T> &d = descs[line];
-    const T ih = (T)d.inv_h, beta = (T)d.beta;
-    const T *un = d.u_out, *wn = d.w_out;
-    const long long snp = d.snp, snv = d.snv;
-    double w[8];
-    int c0;
-    if (method == kCFD) {
-        if (j <= N) {
-            const int n = cfd_Q_row(N, j, &c0, w);
-            T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
-            scratch[(long long)j * st + line] = acc * ih;
+    // block (32 lines, 8): elements j0 .. j0 + 31 of 32 consecutive lines; lane = line reads the
+    // row-major natural fields coalesced.  MFD writes w* and a, which are contiguous along each
+    // line, through shared memory, along each line in turn.
+    __shared__ T tv[32][33], tp[32][33], tu[32][33];
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int line0 = blockIdx.x * 32, line = line0 + x;
+    const int j0 = blockIdx.y * 32;
+    if (line < nlines) {
+        const LineDesc<T> &d = descs[line];
+        const T ih = (T)d.inv_h, beta = (T)d.beta;
+        const T *un = d.u_out, *wn = d.w_out;
+        const long long snp = d.snp, snv = d.snv;
+        double w[8];
+        int c0;
+        for (int jj = y; jj < 32; jj += 8) {
+            const int j = j0 + jj;
+            if (j > N + 1) break;
+            if (method == kCFD) {
+                if (j <= N) {
+                    const int n = cfd_Q_row(N, j, &c0, w);
+                    T acc = T(0);
+                    for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+                    scratch[(long long)j * st + line] = acc * ih;
+                }
+                if (j >= 1 && j <= N - 1) {
+                    const int n = cfd_Qbar_row(N, j, &c0, w);
+                    T acc = T(0);
+                    for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+                    scratch[(long long)(N + j) * st + line] = acc * ih;
+                }
+            } else {
+                if (j <= N) {
+                    const int n = mfd_G_row(N, j, &c0, w);
+                    T acc = T(0);
+                    for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+                    tv[jj][x] = wn[j * snv] - beta * acc * ih;
+                }
+                tu[jj][x] = un[j * snp];
+                if (j >= 1 && j <= N) {
+                    // a = u - alpha (D w)/h (+ source), formed below along the line
+                    const int n = mfd_D_row(N, j - 1, &c0, w);
+                    T acc = T(0);
+                    for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+                    tp[jj][x] = acc;
+                }
+            }
         }
-        if (j >= 1 && j <= N - 1) {
-            const int n = cfd_Qbar_row(N, j, &c0, w);
-            T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
-            scratch[(long long)(N + j) * st + line] = acc * ih;
-        }
-    } else {
-        if (j <= N) {
-            const int n = mfd_G_row(N, j, &c0, w);
-            T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
-            d.v[j * d.sv] = wn[j * snv] - beta * acc * ih;
-        }
+    }
+    if (method == kCFD) return;  // uniform over the block
+    __syncthreads();
+    // lane = element: 8 lines at a time, 32 consecutive elements each
+    for (int l = y; l < 32 && line0 + l < nlines; l += 8) {
+        const LineDesc<T> &dl = descs[line0 + l];
+        const int j = j0 + x;
+        if (j > N + 1) continue;
+        if (j <= N) dl.v[(long long)j * dl.sv] = tv[x][l];
+        T val = tu[x][l];  // j = 0 or N+1: Dirichlet, u itself
         if (j >= 1 && j <= N) {
-            const int n = mfd_D_row(N, j - 1, &c0, w);
-            T acc = T(0);
-            for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
-            T val = un[j * snp] - d.alpha[j * d.sp] * acc * ih;
-            if (j == d.src_k) val += prologue_src(d);
-            d.po[j * d.spo] = val;
-        } else {
-            d.po[(long long)j * d.spo] = un[(long long)j * snp];  // j = 0 or N+1: Dirichlet
+            val = val - dl.alpha[(long long)j * dl.sp] * tp[x][l] * (T)dl.inv_h;
+            if (j == dl.src_k) val += prologue_src(dl);
         }
+        dl.po[(long long)j * dl.spo] = val;
     }
 }
 
@@ -446,17 +469,19 @@ __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, i
 // last kProH values of the factor buffer) join the whole line's factors within kProH rows.
 constexpr int kProR = 64, kProH = 32;
 
+// The forward values of rows r0..r1-1 go to tmp[(r - t0) * ts] and are read back by the
+// backward sweep just before out(r, x) is called for the row.
 template <typename T, typename Out>
 __host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r1, const T *q, long long st,
                                                    const T *lo, const T *cu, const T *id, const T *su_id,
-                                                   T *tmp, long long ts, Out out) {
+                                                   T *tmp, long long ts, Out out, int t0 = 0) {
     const int s = r0 > 0 ? r0 - kProH : 0;
     const int e = r1 + kProH < n ? r1 + kProH : n;
     T dd = T(0);
     for (int r = s; r < r0; ++r) dd = (q[(long long)r * st] - dd) * su_id[r - s];  // start-up rows
     for (int r = r0; r < r1; ++r) {
         dd = (q[(long long)r * st] - lo[r] * dd) * id[r];
-        tmp[(long long)r * ts] = dd;
+        tmp[(long long)(r - t0) * ts] = dd;
     }
     T hh[kProH];
 #pragma unroll
@@ -474,51 +499,67 @@ __host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r
         if (r < e) x = hh[k] - cu[r] * x;
     }
     for (int r = r1 - 1; r >= r0; --r) {
-        x = tmp[(long long)r * ts] - cu[r] * x;
+        x = tmp[(long long)(r - t0) * ts] - cu[r] * x;
         out(r, x);
     }
 }
 
-// grid.y: the chunks of P (N+1 rows) first, then those of Pbar (N-1 rows).
+// grid.y: the chunks of P (N+1 rows) first, then those of Pbar (N-1 rows).  A block is one warp
+// of 32 consecutive lines.  The lines' natural fields are row-major, so lane = line reads them
+// coalesced; the outputs (w*, a) and alpha are contiguous along each line, so they go through
+// shared memory and move along each line in turn, lane = row.
 template <typename T>
-__global__ void prologue_solve_win_kernel(const LineDesc<T> *__restrict__ descs, int nlines, int N, const T *scratch,
-                                          long long st, const T *__restrict__ fac) {
-    const int line = blockIdx.x * blockDim.x + threadIdx.x;
-    if (line >= nlines) return;
-    const LineDesc<T> &d = descs[line];
-    const T beta = (T)d.beta;
-    const T *un = d.u_out, *wn = d.w_out;
-    const long long snp = d.snp, snv = d.snv, spo = d.spo;
+__global__ void __launch_bounds__(32) prologue_solve_win_kernel(const LineDesc<T> *__restrict__ descs, int nlines,
+                                                                int N, const T *scratch, long long st,
+                                                                const T *__restrict__ fac) {
+    __shared__ T tile[kProR][33];  // per line: the forward values, then the chunk's outputs
+    __shared__ T tu[kProR][33];    // Pbar chunks: u at the chunk's nodes
+    const int lane = threadIdx.x;
+    const int line0 = blockIdx.x * 32, line = line0 + lane;
     const int nP = N + 1, nB = N - 1;
     const int chP = (nP + kProR - 1) / kProR;
+    const bool isP = (int)blockIdx.y < chP;
+    const int c = isP ? (int)blockIdx.y : (int)blockIdx.y - chP;
+    const int r0 = c * kProR, r1 = min(isP ? nP : nB, r0 + kProR), nr = r1 - r0;
     const T *su_id = fac + 3 * (N + 1) + 3 * (N - 1);
-    const T *q = scratch + line;
-    if ((int)blockIdx.y < chP) {
-        // P g = (Q u)/h over rows 0..N; w*_r = w_r - beta g_r
-        const int r0 = blockIdx.y * kProR, r1 = min(nP, r0 + kProR);
-        const T *lo = fac, *cu = fac + (N + 1), *id = fac + 2 * (N + 1);
-        T *v = d.v;
-        const long long sv = d.sv;
-        prologue_win_solve<T>(nP, r0, r1, q, st, lo, cu, id, su_id, v, sv,
-                              [&](int r, T g) { v[(long long)r * sv] = wn[(long long)r * snv] - beta * g; });
-    } else {
-        // Pbar e = (Qbar w)/h over nodes 1..N-1 (rows 0..N-2); a_j = u_j - alpha_j e_j (+ source)
-        const int c = blockIdx.y - chP;
-        const int r0 = c * kProR, r1 = min(nB, r0 + kProR);
-        const T *fb = fac + 3 * (N + 1);
-        const T *lo = fb, *cu = fb + (N - 1), *id = fb + 2 * (N - 1);
-        const T *qb = q + (long long)(N + 1) * st;
-        const T src = d.src_k >= 0 ? prologue_src(d) : T(0);
-        T *po = d.po;
-        prologue_win_solve<T>(nB, r0, r1, qb, st, lo, cu, id, su_id, po + spo, spo, [&](int r, T e) {
-            const int j = r + 1;
-            T val = un[(long long)j * snp] - d.alpha[(long long)j * d.sp] * e;
-            if (j == d.src_k) val += src;
-            po[(long long)j * spo] = val;
-        });
-        if (c == 0) {
-            po[0] = un[0];
-            po[(long long)N * spo] = un[(long long)N * snp];
+    if (line < nlines) {
+        const LineDesc<T> &d = descs[line];
+        const T beta = (T)d.beta;
+        const T *un = d.u_out, *wn = d.w_out;
+        const long long snp = d.snp, snv = d.snv;
+        const T *q = scratch + line;
+        if (isP) {
+            // P g = (Q u)/h over rows 0..N; w*_r = w_r - beta g_r
+            const T *lo = fac, *cu = fac + (N + 1), *id = fac + 2 * (N + 1);
+            prologue_win_solve<T>(nP, r0, r1, q, st, lo, cu, id, su_id, &tile[0][lane], 33,
+                                  [&](int r, T g) { tile[r - r0][lane] = wn[(long long)r * snv] - beta * g; }, r0);
+        } else {
+            // Pbar e = (Qbar w)/h over nodes 1..N-1 (rows 0..N-2); a_j = u_j - alpha_j e_j (+ source)
+            const T *fb = fac + 3 * (N + 1);
+            const T *lo = fb, *cu = fb + (N - 1), *id = fb + 2 * (N - 1);
+            const T *qb = q + (long long)(N + 1) * st;
+            prologue_win_solve<T>(nB, r0, r1, qb, st, lo, cu, id, su_id, &tile[0][lane], 33, [&](int r, T e) {
+                tile[r - r0][lane] = e;
+                tu[r - r0][lane] = un[(long long)(r + 1) * snp];
+            }, r0);
+            if (c == 0) {
+                d.po[0] = un[0];
+                d.po[(long long)N * d.spo] = un[(long long)N * snp];
+            }
+        }
+    }
+    __syncwarp();
+    for (int l = 0; l < 32 && line0 + l < nlines; ++l) {
+        const LineDesc<T> &dl = descs[line0 + l];
+        if (isP) {
+            for (int k = lane; k < nr; k += 32) dl.v[(long long)(r0 + k) * dl.sv] = tile[k][l];
+        } else {
+            for (int k = lane; k < nr; k += 32) {
+                const long long j = r0 + k + 1;
+                T val = tu[k][l] - dl.alpha[j * dl.sp] * tile[k][l];
+                if (j == dl.src_k) val += prologue_src(dl);
+                dl.po[j * dl.spo] = val;
+            }
         }
     }
 }
@@ -565,12 +606,12 @@ template <typename T>
 cudaError_t launch_prologue_lines(const LineDesc<T> *d, int nlines, int N, int method, const T *fac, T *scratch,
                                   long long st, cudaStream_t s) {
     if (nlines <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((nlines + 31) / 32), (unsigned)((N + 2 + 7) / 8));
+    dim3 grid((unsigned)((nlines + 31) / 32), (unsigned)((N + 2 + 31) / 32));
     prologue_stencil_kernel<T><<<grid, dim3(32, 8), 0, s>>>(d, nlines, N, method, scratch, st);
     if (method == kCFD) {
         const unsigned chunks = (unsigned)((N + 1 + kProR - 1) / kProR + (N - 1 + kProR - 1) / kProR);
-        prologue_solve_win_kernel<T><<<dim3((unsigned)((nlines + 127) / 128), chunks), 128, 0, s>>>(d, nlines, N,
-                                                                                                 scratch, st, fac);
+        prologue_solve_win_kernel<T><<<dim3((unsigned)((nlines + 31) / 32), chunks), 32, 0, s>>>(d, nlines, N,
+                                                                                              scratch, st, fac);
     }
     return cudaGetLastError();
 }
