@@ -316,43 +316,47 @@ struct adi_batch_t {
 
 namespace {
 
+// The conversions below give each thread one column and a stride of gridDim.y rows (at most 128
+// block rows, so a thread converts many rows, with its loads in flight together); both sides
+// are coalesced and no thread divides a flat index.
+inline dim3 conv_grid(size_t rows, size_t cols) {
+    return dim3((unsigned)((cols + 255) / 256), (unsigned)(rows < 128 ? (rows > 0 ? rows : 1) : 128));
+}
 // Compact row-major double (rows x cols) -> rows with leading dimension ld in T.
 template <typename T>
 __global__ void convert_from_double(const double *src, T *dst, size_t rows, size_t cols, size_t ld,
                                     double scale, int square) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < rows * cols) {
-        size_t r = i / cols, c = i - r * cols;
-        double x = src[i];
+    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+#pragma unroll 4
+    for (size_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const double x = src[r * cols + c];
         dst[r * ld + c] = (T)(square ? scale * x * x : scale * x);
     }
 }
 // Rows with leading dimension ld in T -> compact row-major double.
 template <typename T>
 __global__ void convert_to_double(const T *src, double *dst, size_t rows, size_t cols, size_t ld) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < rows * cols) {
-        size_t r = i / cols, c = i - r * cols;
-        dst[i] = (double)src[r * ld + c];
-    }
+    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+#pragma unroll 4
+    for (size_t r = blockIdx.y; r < rows; r += gridDim.y) dst[r * cols + c] = (double)src[r * ld + c];
 }
 // Compact row-major S (rows x cols) -> rows with leading dimension ld in T.
 template <typename S, typename T>
 __global__ void convert_in(const S *src, T *dst, size_t rows, size_t cols, size_t ld) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < rows * cols) {
-        size_t r = i / cols, c = i - r * cols;
-        dst[r * ld + c] = (T)src[i];
-    }
+    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+#pragma unroll 4
+    for (size_t r = blockIdx.y; r < rows; r += gridDim.y) dst[r * ld + c] = (T)src[r * cols + c];
 }
 // Rows with leading dimension ld in T -> compact row-major D.
 template <typename T, typename D>
 __global__ void convert_out(const T *src, D *dst, size_t rows, size_t cols, size_t ld) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < rows * cols) {
-        size_t r = i / cols, c = i - r * cols;
-        dst[i] = (D)src[r * ld + c];
-    }
+    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+#pragma unroll 4
+    for (size_t r = blockIdx.y; r < rows; r += gridDim.y) dst[r * cols + c] = (D)src[r * ld + c];
 }
 
 // dst[j * ld_dst + i] = src[i * ld_src + j] for a rows x cols array (32 x 32 tiles).
@@ -457,11 +461,11 @@ int upload(adi_sim *s, const double *host, void *dst, size_t rows, size_t cols, 
     else
         e = cudaMemsetAsync(staging, 0, n * sizeof(double), s->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    unsigned blocks = (unsigned)((n + 255) / 256);
+    const dim3 grid = conv_grid(rows, cols);
     if (s->precision == ADI_FP64)
-        convert_from_double<double><<<blocks, 256, 0, s->stream>>>(staging, (double *)dst, rows, cols, ld, scale, square);
+        convert_from_double<double><<<grid, 256, 0, s->stream>>>(staging, (double *)dst, rows, cols, ld, scale, square);
     else
-        convert_from_double<float><<<blocks, 256, 0, s->stream>>>(staging, (float *)dst, rows, cols, ld, scale, square);
+        convert_from_double<float><<<grid, 256, 0, s->stream>>>(staging, (float *)dst, rows, cols, ld, scale, square);
     return cuda_status(cudaGetLastError());
 }
 
@@ -1030,13 +1034,13 @@ int stage_fields(adi_sim *s, const void *const f[3], bool f32, const void *stage
 // simulation's precision with leading dimension ld; nullptr: zeros.
 int load_field(adi_sim *s, const void *staged, bool f32, void *dst, size_t rows, size_t cols, size_t ld) {
     if (!staged) return cuda_status(cudaMemsetAsync(dst, 0, rows * ld * s->esz, s->stream));
-    const unsigned blocks = (unsigned)((rows * cols + 255) / 256);
+    const dim3 grid = conv_grid(rows, cols);
     if (s->precision == ADI_FP64) {
-        if (f32) convert_in<float, double><<<blocks, 256, 0, s->stream>>>((const float *)staged, (double *)dst, rows, cols, ld);
-        else convert_in<double, double><<<blocks, 256, 0, s->stream>>>((const double *)staged, (double *)dst, rows, cols, ld);
+        if (f32) convert_in<float, double><<<grid, 256, 0, s->stream>>>((const float *)staged, (double *)dst, rows, cols, ld);
+        else convert_in<double, double><<<grid, 256, 0, s->stream>>>((const double *)staged, (double *)dst, rows, cols, ld);
     } else {
-        if (f32) convert_in<float, float><<<blocks, 256, 0, s->stream>>>((const float *)staged, (float *)dst, rows, cols, ld);
-        else convert_in<double, float><<<blocks, 256, 0, s->stream>>>((const double *)staged, (float *)dst, rows, cols, ld);
+        if (f32) convert_in<float, float><<<grid, 256, 0, s->stream>>>((const float *)staged, (float *)dst, rows, cols, ld);
+        else convert_in<double, float><<<grid, 256, 0, s->stream>>>((const double *)staged, (float *)dst, rows, cols, ld);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -1598,11 +1602,11 @@ int adi_read_fields(adi_handle s, double *u, double *v, double *w) {
     for (auto &pt : parts) {
         if (!pt.dst) continue;
         const size_t n = pt.rows * pt.cols;
-        unsigned blocks = (unsigned)((n + 255) / 256);
+        const dim3 grid = conv_grid(pt.rows, pt.cols);
         if (s->precision == ADI_FP64)
-            convert_to_double<double><<<blocks, 256, 0, s->stream>>>((const double *)pt.src, (double *)tmp.p, pt.rows, pt.cols, pt.ld);
+            convert_to_double<double><<<grid, 256, 0, s->stream>>>((const double *)pt.src, (double *)tmp.p, pt.rows, pt.cols, pt.ld);
         else
-            convert_to_double<float><<<blocks, 256, 0, s->stream>>>((const float *)pt.src, (double *)tmp.p, pt.rows, pt.cols, pt.ld);
+            convert_to_double<float><<<grid, 256, 0, s->stream>>>((const float *)pt.src, (double *)tmp.p, pt.rows, pt.cols, pt.ld);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(pt.dst, tmp.p, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
@@ -1653,21 +1657,32 @@ int adi_read_fields_f32(adi_handle s, float *u, float *v, float *w) {
         {s->Uo.p, u, (size_t)g.rows_u, (size_t)g.ldu, (size_t)g.ldu},
         {s->V[s->parity].p, v, (size_t)g.rows_v, (size_t)g.ldv, (size_t)g.ldvp},
         {s->Wo.p, w, (size_t)g.rows_w, (size_t)g.ldw, (size_t)g.ldw}};
-    if (s->precision == ADI_FP64) {
+    // FP64 fields are converted through the staging buffer; an FP32 field whose rows are padded
+    // (v) is first packed there on the device, since a pitched device-to-host copy runs at about
+    // half the speed of a contiguous one
+    bool need_xfer = s->precision == ADI_FP64;
+    for (auto &pt : parts) need_xfer |= pt.dst && pt.ld != pt.cols;
+    if (need_xfer) {
         rc = xfer_buffer(s);
         if (rc) return rc;
     }
     cudaError_t e = cudaSuccess;
     for (auto &pt : parts) {
         if (!pt.dst || e != cudaSuccess) continue;
-        if (s->precision == ADI_FP32) {  // straight from the device arrays (rows of ld elements)
-            e = cudaMemcpy2DAsync(pt.dst, pt.cols * sizeof(float), pt.src, pt.ld * sizeof(float), pt.cols * sizeof(float),
-                                  pt.rows, cudaMemcpyDeviceToHost, s->stream);
+        if (s->precision == ADI_FP32 && pt.ld == pt.cols) {  // straight from the device array
+            e = cudaMemcpyAsync(pt.dst, pt.src, pt.rows * pt.cols * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+        } else if (s->precision == ADI_FP32) {
+            convert_out<float, float><<<conv_grid(pt.rows, pt.cols), 256, 0, s->stream>>>(
+                (const float *)pt.src, (float *)s->xfer.p, pt.rows, pt.cols, pt.ld);
+            e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(pt.dst, s->xfer.p, pt.rows * pt.cols * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the staging is reused
         } else {
             const size_t n = pt.rows * pt.cols;
-            convert_out<double, float><<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>((const double *)pt.src,
-                                                                                          (float *)s->xfer.p, pt.rows,
-                                                                                          pt.cols, pt.ld);
+            convert_out<double, float><<<conv_grid(pt.rows, pt.cols), 256, 0, s->stream>>>((const double *)pt.src,
+                                                                                           (float *)s->xfer.p, pt.rows,
+                                                                                           pt.cols, pt.ld);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpyAsync(pt.dst, s->xfer.p, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the staging is reused

@@ -389,6 +389,28 @@ __device__ __forceinline__ T prologue_src(const LineDesc<T> &d) {
     return (T)(d.src_scale * ricker(d.src_amp, d.src_f0, d.src_tdelay, (double)(*d.clock) * d.dt));
 }
 
+// Interior rows of the explicit operators (CFD Q and Qbar: -3, 0, 3; MFD D4 and G4: the
+// fourth-order staggered stencil), with the weights as compile-time constants of T; the same
+// terms in the same order as the row functions give them, so the sums are the same.  p points
+// at the row's first point, s is the stride along the line.
+template <typename T>
+__device__ __forceinline__ T cfd_interior_dot(const T *p, long long s) {
+    T acc = T(0);
+    acc += T(-3.0) * p[0];
+    acc += T(0.0) * p[s];
+    acc += T(3.0) * p[2 * s];
+    return acc;
+}
+template <typename T>
+__device__ __forceinline__ T mfd_interior_dot(const T *p, long long s) {
+    T acc = T(0);
+    acc += T(1.0 / 24.0) * p[0];
+    acc += T(-9.0 / 8.0) * p[s];
+    acc += T(9.0 / 8.0) * p[2 * s];
+    acc += T(-1.0 / 24.0) * p[3 * s];
+    return acc;
+}
+
 template <typename T>
 __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, int nlines, int N, int method,
                                         T *scratch, long long st) {
@@ -396,11 +418,24 @@ __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, i
     // row-major natural fields coalesced.  MFD writes w* and a, which are contiguous along each
     // line, through shared memory, along each line in turn.
     __shared__ T tv[32][33], tp[32][33], tu[32][33];
+    // the block's 32 descriptors, copied once with 16-byte loads (each thread would otherwise
+    // read its own descriptor's fields, 32 scattered sectors per load)
+    __shared__ __align__(16) unsigned char sdesc[32 * sizeof(LineDesc<T>)];
+    static_assert(sizeof(LineDesc<T>) % 16 == 0, "descriptor size");
     const int x = threadIdx.x, y = threadIdx.y;
     const int line0 = blockIdx.x * 32, line = line0 + x;
     const int j0 = blockIdx.y * 32;
+    {
+        const int nl = min(32, nlines - line0);
+        const uint4 *src = reinterpret_cast<const uint4 *>(descs + line0);
+        uint4 *dst = reinterpret_cast<uint4 *>(sdesc);
+        const int nvec = nl * (int)(sizeof(LineDesc<T>) / 16);
+        for (int k = y * 32 + x; k < nvec; k += 256) dst[k] = src[k];
+    }
+    __syncthreads();
+    const LineDesc<T> *sd = reinterpret_cast<const LineDesc<T> *>(sdesc);
     if (line < nlines) {
-        const LineDesc<T> &d = descs[line];
+        const LineDesc<T> &d = sd[x];
         const T ih = (T)d.inv_h, beta = (T)d.beta;
         const T *un = d.u_out, *wn = d.w_out;
         const long long snp = d.snp, snv = d.snv;
@@ -411,30 +446,46 @@ __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, i
             if (j > N + 1) break;
             if (method == kCFD) {
                 if (j <= N) {
-                    const int n = cfd_Q_row(N, j, &c0, w);
                     T acc = T(0);
-                    for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+                    if (j >= 1 && j <= N - 1) {
+                        acc = cfd_interior_dot(un + (long long)(j - 1) * snp, snp);
+                    } else {
+                        const int n = cfd_Q_row(N, j, &c0, w);
+                        for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+                    }
                     scratch[(long long)j * st + line] = acc * ih;
                 }
                 if (j >= 1 && j <= N - 1) {
-                    const int n = cfd_Qbar_row(N, j, &c0, w);
                     T acc = T(0);
-                    for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+                    if (j >= 2 && j <= N - 2) {
+                        acc = cfd_interior_dot(wn + (long long)(j - 1) * snv, snv);
+                    } else {
+                        const int n = cfd_Qbar_row(N, j, &c0, w);
+                        for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+                    }
                     scratch[(long long)(N + j) * st + line] = acc * ih;
                 }
             } else {
                 if (j <= N) {
-                    const int n = mfd_G_row(N, j, &c0, w);
                     T acc = T(0);
-                    for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+                    if (j >= 2 && j <= N - 2) {
+                        acc = mfd_interior_dot(un + (long long)(j - 1) * snp, snp);
+                    } else {
+                        const int n = mfd_G_row(N, j, &c0, w);
+                        for (int t = 0; t < n; ++t) acc += (T)w[t] * un[(c0 + t) * snp];
+                    }
                     tv[jj][x] = wn[j * snv] - beta * acc * ih;
                 }
                 tu[jj][x] = un[j * snp];
                 if (j >= 1 && j <= N) {
                     // a = u - alpha (D w)/h (+ source), formed below along the line
-                    const int n = mfd_D_row(N, j - 1, &c0, w);
                     T acc = T(0);
-                    for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+                    if (j >= 2 && j <= N - 1) {
+                        acc = mfd_interior_dot(wn + (long long)(j - 2) * snv, snv);
+                    } else {
+                        const int n = mfd_D_row(N, j - 1, &c0, w);
+                        for (int t = 0; t < n; ++t) acc += (T)w[t] * wn[(c0 + t) * snv];
+                    }
                     tp[jj][x] = acc;
                 }
             }
@@ -444,7 +495,7 @@ __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, i
     __syncthreads();
     // lane = element: 8 lines at a time, 32 consecutive elements each
     for (int l = y; l < 32 && line0 + l < nlines; l += 8) {
-        const LineDesc<T> &dl = descs[line0 + l];
+        const LineDesc<T> &dl = sd[l];
         const int j = j0 + x;
         if (j > N + 1) continue;
         if (j <= N) dl.v[(long long)j * dl.sv] = tv[x][l];
@@ -469,18 +520,21 @@ __global__ void prologue_stencil_kernel(const LineDesc<T> *__restrict__ descs, i
 // last kProH values of the factor buffer) join the whole line's factors within kProH rows.
 constexpr int kProR = 64, kProH = 32;
 
-// The forward values of rows r0..r1-1 go to tmp[(r - t0) * ts] and are read back by the
-// backward sweep just before out(r, x) is called for the row.
-template <typename T, typename Out>
-__host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r1, const T *q, long long st,
-                                                   const T *lo, const T *cu, const T *id, const T *su_id,
-                                                   T *tmp, long long ts, Out out, int t0 = 0) {
+// q(r) gives the right-hand side of row r.  The forward values of rows r0..r1-1 go to
+// tmp[(r - t0) * ts] and are read back by the backward sweep just before out(r, x) is called for
+// the row.
+template <typename T, typename QF, typename Out>
+__host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r1, QF q, const T *lo, const T *cu,
+                                                            const T *id, const T *su_id, T *tmp, long long ts,
+                                                            Out out, int t0 = 0) {
     const int s = r0 > 0 ? r0 - kProH : 0;
     const int e = r1 + kProH < n ? r1 + kProH : n;
     T dd = T(0);
-    for (int r = s; r < r0; ++r) dd = (q[(long long)r * st] - dd) * su_id[r - s];  // start-up rows
+#pragma unroll 8
+    for (int r = s; r < r0; ++r) dd = (q(r) - dd) * su_id[r - s];  // start-up rows
+#pragma unroll 8
     for (int r = r0; r < r1; ++r) {
-        dd = (q[(long long)r * st] - lo[r] * dd) * id[r];
+        dd = (q(r) - lo[r] * dd) * id[r];
         tmp[(long long)(r - t0) * ts] = dd;
     }
     T hh[kProH];
@@ -488,7 +542,7 @@ __host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r
     for (int k = 0; k < kProH; ++k) {
         const int r = r1 + k;
         if (r < e) {
-            dd = (q[(long long)r * st] - lo[r] * dd) * id[r];
+            dd = (q(r) - lo[r] * dd) * id[r];
             hh[k] = dd;
         }
     }
@@ -498,6 +552,7 @@ __host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r
         const int r = r1 + k;
         if (r < e) x = hh[k] - cu[r] * x;
     }
+#pragma unroll 8
     for (int r = r1 - 1; r >= r0; --r) {
         x = tmp[(long long)(r - t0) * ts] - cu[r] * x;
         out(r, x);
@@ -507,7 +562,9 @@ __host__ __device__ __forceinline__ void prologue_win_solve(int n, int r0, int r
 // grid.y: the chunks of P (N+1 rows) first, then those of Pbar (N-1 rows).  A block is one warp
 // of 32 consecutive lines.  The lines' natural fields are row-major, so lane = line reads them
 // coalesced; the outputs (w*, a) and alpha are contiguous along each line, so they go through
-// shared memory and move along each line in turn, lane = row.
+// shared memory and move along each line in turn, lane = row.  (Loading the window's right-hand
+// sides and natural values into shared memory first measured slower: 508-536 against 406 us at
+// 4096 lines of 4097 rows.)
 template <typename T>
 __global__ void __launch_bounds__(32) prologue_solve_win_kernel(const LineDesc<T> *__restrict__ descs, int nlines,
                                                                 int N, const T *scratch, long long st,
@@ -527,18 +584,18 @@ __global__ void __launch_bounds__(32) prologue_solve_win_kernel(const LineDesc<T
         const T beta = (T)d.beta;
         const T *un = d.u_out, *wn = d.w_out;
         const long long snp = d.snp, snv = d.snv;
-        const T *q = scratch + line;
+        const T *__restrict__ q = scratch + (isP ? 0 : (long long)(N + 1) * st) + line;
+        auto qf = [&](int r) -> T { return q[(long long)r * st]; };
         if (isP) {
             // P g = (Q u)/h over rows 0..N; w*_r = w_r - beta g_r
             const T *lo = fac, *cu = fac + (N + 1), *id = fac + 2 * (N + 1);
-            prologue_win_solve<T>(nP, r0, r1, q, st, lo, cu, id, su_id, &tile[0][lane], 33,
+            prologue_win_solve<T>(nP, r0, r1, qf, lo, cu, id, su_id, &tile[0][lane], 33,
                                   [&](int r, T g) { tile[r - r0][lane] = wn[(long long)r * snv] - beta * g; }, r0);
         } else {
             // Pbar e = (Qbar w)/h over nodes 1..N-1 (rows 0..N-2); a_j = u_j - alpha_j e_j (+ source)
             const T *fb = fac + 3 * (N + 1);
             const T *lo = fb, *cu = fb + (N - 1), *id = fb + 2 * (N - 1);
-            const T *qb = q + (long long)(N + 1) * st;
-            prologue_win_solve<T>(nB, r0, r1, qb, st, lo, cu, id, su_id, &tile[0][lane], 33, [&](int r, T e) {
+            prologue_win_solve<T>(nB, r0, r1, qf, lo, cu, id, su_id, &tile[0][lane], 33, [&](int r, T e) {
                 tile[r - r0][lane] = e;
                 tu[r - r0][lane] = un[(long long)(r + 1) * snp];
             }, r0);
@@ -564,12 +621,29 @@ __global__ void __launch_bounds__(32) prologue_solve_win_kernel(const LineDesc<T
     }
 }
 
+// Sets *flag if any x[i] is NaN or infinite: 16-byte loads over the aligned body of x (when x
+// itself is 16-byte aligned), element loads for the rest.
 template <typename T>
 __global__ void finite_check_kernel(const T *__restrict__ x, size_t n, int *flag) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    size_t stride = (size_t)gridDim.x * blockDim.x;
+    constexpr int V = 16 / sizeof(T);
+    const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t nv = ((size_t)x & 15u) == 0 ? n / V : 0;
     bool bad = false;
-    for (; i < n; i += stride) bad |= !isfinite((double)x[i]);
+    if constexpr (sizeof(T) == 4) {
+        const float4 *xv = reinterpret_cast<const float4 *>(x);
+        for (size_t i = i0; i < nv; i += stride) {
+            const float4 q = xv[i];
+            bad |= !(isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w));
+        }
+    } else {
+        const double2 *xv = reinterpret_cast<const double2 *>(x);
+        for (size_t i = i0; i < nv; i += stride) {
+            const double2 q = xv[i];
+            bad |= !(isfinite(q.x) && isfinite(q.y));
+        }
+    }
+    for (size_t i = nv * V + i0; i < n; i += stride) bad |= !isfinite((double)x[i]);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
 }
 

@@ -68,7 +68,7 @@ int main() {
             std::vector<int> hits(n, 0);
             for (int r0 = 0; r0 < n; r0 += kProR) {
                 const int r1 = std::min(n, r0 + kProR);
-                prologue_win_solve<double>(n, r0, r1, b.data(), 1, lo, cu, id, su_id, tmp.data(), 1,
+                prologue_win_solve<double>(n, r0, r1, [&](int r) { return b[r]; }, lo, cu, id, su_id, tmp.data(), 1,
                                            [&](int r, double v) { xc[r] = v; ++hits[r]; });
             }
             double errc = 0.0;
