@@ -222,7 +222,10 @@ int adi_sync(adi_handle sim);
  * buffers with the shapes above (any pointer may be NULL to skip that field): pressure and
  * the two velocity components of Eq. 1 at the mesh points of Sec. 2.1 (CFD: all on nodes) or
  * Sec. 2.2 (MFD: pressure at cell centres and edges, v on x-faces, w on y-faces), at the
- * handle's current time.  Errors: the handle's sticky error, ADI_ECUDA.
+ * handle's current time.  Fields that need converting or packing (FP64 arrays, a padded
+ * velocity array) pass through a device staging buffer of three fields in FP64, allocated on
+ * its first use and kept until adi_destroy.  Errors: the handle's sticky error, ADI_ENOMEM (the
+ * staging buffer), ADI_ECUDA.
  */
 int adi_read_fields(adi_handle sim, double *u, double *v, double *w);
 
