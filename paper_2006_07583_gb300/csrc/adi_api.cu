@@ -36,6 +36,7 @@
 
 #include "../../include/adi.h"
 #include "adi_internal.h"
+#include "adi_line.cuh"
 #include "adi_ops.cuh"
 
 using namespace adi;
@@ -191,6 +192,9 @@ struct Plan {
     // carried-pressure transposes after each stage, one array per member: [dir]
     DevBuf tdesc[2];
     int tcount[2] = {0, 0}, trows[2] = {0, 0}, tcols[2] = {0, 0};
+    // natural fields after a stage 2 that writes them: one record per member, per plan parity
+    DevBuf ndesc[2];
+    int ncount = 0, nrows = 0, ncols = 0;
     DevBuf fault;                            // set by a factored launch whose wait ran out
     // time-harmonic walls and forcing of the members that have them (after each stage)
     DevBuf hdesc;
@@ -237,7 +241,9 @@ void plan_free(Plan &p) {
     for (int d = 0; d < 2; ++d) {
         dev_free(p.tdesc[d]);
         p.tcount[d] = p.trows[d] = p.tcols[d] = 0;
+        dev_free(p.ndesc[d]);
     }
+    p.ncount = p.nrows = p.ncols = 0;
     dev_free(p.scratch);
     dev_free(p.fault);
     dev_free(p.hdesc);
@@ -357,6 +363,62 @@ __global__ void convert_out(const T *src, D *dst, size_t rows, size_t cols, size
     if (c >= cols) return;
 #pragma unroll 4
     for (size_t r = blockIdx.y; r < rows; r += gridDim.y) dst[r * cols + c] = (D)src[r * ld + c];
+}
+
+// The natural fields after a step, from the carried state of its stage 2: a y-line solve leaves
+// a = 2u - C (+ the point source's dt/2 f) and w*' = 2w - w*, and keeps its inputs C and w*, so
+// u = (a + C)/2 and w = (w*' + w*)/2 on every point the y-lines solve (CFD: u on nodes 1..N-1,
+// MFD: cells 1..N; w on 0..N; columns 1..pix).  One record per member and plan parity.
+struct NatDesc {
+    const void *a, *c;        // A[3] (a) and A[1] (C), column-major: column j at j * ldc
+    const void *wn, *wi;      // w*' (the stage's output) and w* (its input), column j at j * ldwc
+    void *uo, *wo;            // natural u (row-major, ldu) and w (row-major, ldw)
+    const long long *clock;   // the member's step clock (for the point source)
+    int ldc, ldwc, ldu, ldw;
+    int j1;                   // columns 1 .. j1 - 1
+    int ku0, ku1, kw1;        // u rows [ku0, ku1), w rows [0, kw1)
+    int src_i, src_j;         // the point source's row and column, or -1
+    int clock_ahead;          // 1: the clock has not yet advanced past this step (harmonic walls)
+    double dt, src_amp, src_f0, src_td, src_scale;
+};
+
+// blockIdx.z: the member; a 32 x 32 tile of (row k, column j) per block.  The carried arrays are
+// read along their columns (lane = row) and the natural ones written along their rows (lane =
+// column), through shared memory, so both sides are coalesced.
+template <typename T>
+__global__ void naturalize_kernel(const NatDesc *__restrict__ nd) {
+    __shared__ T tu[32][33], tw[32][33];
+    const NatDesc d = nd[blockIdx.z];
+    const int k0 = blockIdx.y * 32, jb = blockIdx.x * 32;
+    if (k0 >= max(d.ku1, d.kw1) || jb >= d.j1) return;  // uniform over the block
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const T *a = (const T *)d.a, *c = (const T *)d.c, *wn = (const T *)d.wn, *wi = (const T *)d.wi;
+    T src = T(0);
+    if (d.src_j >= 0)
+        src = (T)(d.src_scale *
+                  ricker(d.src_amp, d.src_f0, d.src_td, (double)(*d.clock + d.clock_ahead) * d.dt));
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int j = jb + jj, k = k0 + tx;
+        if (j < 1 || j >= d.j1) continue;
+        if (k >= d.ku0 && k < d.ku1) {
+            const long long o = (long long)j * d.ldc + k;
+            T u = T(0.5) * (a[o] + c[o]);
+            if (k == d.src_i && j == d.src_j) u -= T(0.5) * src;
+            tu[jj][tx] = u;
+        }
+        if (k < d.kw1) {
+            const long long o = (long long)j * d.ldwc + k;
+            tw[jj][tx] = T(0.5) * (wn[o] + wi[o]);
+        }
+    }
+    __syncthreads();
+    T *uo = (T *)d.uo, *wo = (T *)d.wo;
+    for (int kk = ty; kk < 32; kk += 8) {
+        const int k = k0 + kk, j = jb + tx;
+        if (j < 1 || j >= d.j1) continue;
+        if (k >= d.ku0 && k < d.ku1) uo[(long long)k * d.ldu + j] = tu[tx][kk];
+        if (k < d.kw1) wo[(long long)k * d.ldw + j] = tw[tx][kk];
+    }
 }
 
 // dst[j * ld_dst + i] = src[i * ld_src + j] for a rows x cols array (32 x 32 tiles).
@@ -700,6 +762,37 @@ int plan_build(Plan &p, const std::vector<adi_sim *> &members, cudaStream_t stre
         if (!rc) rc = cuda_status(cudaMemcpyAsync(p.tdesc[dir].p, td.data(), td.size() * sizeof(TDesc),
                                                   cudaMemcpyHostToDevice, stream));
     }
+    // the natural fields' records (member parity s->parity ^ q at plan parity q)
+    for (int q = 0; q < 2 && !rc; ++q) {
+        std::vector<NatDesc> nd;
+        for (adi_sim *s : members) {
+            const Geometry &g = s->g;
+            const int pm = s->parity ^ q;
+            NatDesc d;
+            std::memset(&d, 0, sizeof(d));
+            d.a = s->A[3].p; d.c = s->A[1].p;
+            d.wn = s->W[1 - pm].p; d.wi = s->W[pm].p;
+            d.uo = s->Uo.p; d.wo = s->Wo.p;
+            d.clock = (const long long *)s->clock.p;
+            d.ldc = g.ldc; d.ldwc = g.ldwc; d.ldu = g.ldu; d.ldw = g.ldw;
+            d.j1 = 1 + g.pix;
+            d.ku0 = 1;
+            d.ku1 = g.method == ADI_CFD ? g.ny : g.ny + 1;
+            d.kw1 = g.ny + 1;
+            d.src_i = s->src_on ? s->src_i : -1;
+            d.src_j = s->src_on ? s->src_j : -1;
+            d.clock_ahead = s->harm_on ? 1 : 0;
+            d.dt = s->dt; d.src_amp = s->src_amp; d.src_f0 = s->src_f0; d.src_td = s->src_td;
+            d.src_scale = s->dt / (2.0 * s->h * s->h);
+            p.nrows = std::max(p.nrows, std::max(d.ku1, d.kw1));
+            p.ncols = std::max(p.ncols, d.j1);
+            nd.push_back(d);
+        }
+        p.ncount = (int)nd.size();
+        rc = dev_alloc(p.ndesc[q], nd.size() * sizeof(NatDesc));
+        if (!rc) rc = cuda_status(cudaMemcpyAsync(p.ndesc[q].p, nd.data(), nd.size() * sizeof(NatDesc),
+                                                  cudaMemcpyHostToDevice, stream));
+    }
     // the harmonic records of the members with time-harmonic walls
     if (!rc) {
         std::vector<HarmDesc> hd;
@@ -761,23 +854,31 @@ template <typename T>
 cudaError_t enqueue_stage(const Plan &p, int q, int dir, int natural, cudaStream_t stream, cudaEvent_t ev0,
                           cudaEvent_t ev1) {
     cudaError_t e = ev0 ? cudaEventRecord(ev0, stream) : cudaSuccess;
-    // members with absorbing layers need their natural fields after every step
-    int nat = dir == 1 ? (natural || !p.sponges.empty() ? 1 : 0) : 0;
+    // members with absorbing layers need their natural fields after every step; the line solves
+    // leave them to naturalize_kernel below (writing them from the line kernels would put one
+    // scattered element per lane into the row-major natural arrays)
+    const int nat = dir == 1 ? (natural || !p.sponges.empty() ? 1 : 0) : 0;
     if (e == cudaSuccess && p.v1n[dir])
         e = launch_line_solve_v1<T>((const LineDesc<T> *)p.v1d[q][dir].p, p.v1n[dir], (T *)p.scratch.p,
-                                    p.scratch_stride, nat, stream);
+                                    p.scratch_stride, 0, stream);
     for (int v = 0; v < kFacVariants && e == cudaSuccess; ++v)
         if (p.nfgroups[dir][v])
             e = launch_line_solve_factored<T>((const LineDesc<T> *)p.fd[q][dir].p,
                                               (const FacGroup *)p.fgroups[dir][v].p, p.nfgroups[dir][v], v,
-                                              p.fstage[dir][v], p.fstages[dir][v], p.fgrid[dir][v], nat,
+                                              p.fstage[dir][v], p.fstages[dir][v], p.fgrid[dir][v], 0,
                                               (int *)p.fault.p, stream);
     for (int m = 0; m < 2 && e == cudaSuccess; ++m)
         if (p.ngroups[dir][m])
             e = launch_line_solve_chunked<T>((const LineDesc<T> *)p.cd[q][dir].p,
                                              (const int4 *)p.groups[dir][m].p, p.ngroups[dir][m], m,
-                                             p.smem[dir][m], nat, stream);
+                                             p.smem[dir][m], 0, stream);
     if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, stream);
+    // natural u and w from the carried state, before anything moves or changes it
+    if (e == cudaSuccess && nat && p.ncount) {
+        dim3 grid((unsigned)((p.ncols + 31) / 32), (unsigned)((p.nrows + 31) / 32), (unsigned)p.ncount);
+        naturalize_kernel<T><<<grid, dim3(32, 8), 0, stream>>>((const NatDesc *)p.ndesc[q].p);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && p.tcount[dir]) {
         if (sizeof(T) == 4) {
             dim3 grid((unsigned)((p.tcols[dir] + 63) / 64), (unsigned)((p.trows[dir] + 63) / 64), (unsigned)p.tcount[dir]);
