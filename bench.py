@@ -395,10 +395,10 @@ def main():
            "gpu_launches": 2 * K * (len({sp.method for sp in specs}) + 1)}
 
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3), f32=esz == 4, overlap=True)
-        out["e2e_sequential"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3), f32=esz == 4)
+        out["e2e"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 8), f32=esz == 4, overlap=True)
+        out["e2e_sequential"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 8), f32=esz == 4)
         if esz == 4:
-            out["e2e_fp64_host"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 3), f32=False)
+            out["e2e_fp64_host"] = e2e_leg(adi, torch, sims, batch, specs, min(K, 8), f32=False)
     if rank == 0 and not args.no_fp64:
         out["fp64_plain"] = fp64_plain(adi, args.side)
     batch.close()
